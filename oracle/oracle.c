@@ -1,0 +1,279 @@
+/*
+ * CPU oracle: plain, slow, obviously correct.  TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Cited passages are sections, figures and tables of Pan, Pearce, Owens,
+ * "Scalable Breadth-First Search on a GPU Cluster" (arXiv 1803.03922).
+ * Nothing here is blocked, fused or reordered beyond the definitions.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+struct orc_graph {
+  int32_t n;
+  int64_t nnz;
+  int64_t* off; /* n+1 */
+  int32_t* col; /* nnz, each row ascending, no duplicates, no self-loops */
+};
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* Sec. II-B: the graph is symmetric; Sec. VI-A.3: the undirected graph is made
+ * by edge doubling.  Self-loops are dropped and duplicate pairs kept once. */
+orc_graph* orc_graph_build(int32_t n, int64_t m, const int32_t* src, const int32_t* dst) {
+  if (n <= 0 || m < 0 || (m > 0 && (!src || !dst))) return NULL;
+  for (int64_t e = 0; e < m; ++e)
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return NULL;
+
+  int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!cnt) return NULL;
+  /* step 1: count both directions of every non-loop edge */
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t u = src[e], v = dst[e];
+    if (u == v) continue;
+    cnt[u] += 1;
+    cnt[v] += 1;
+  }
+  /* step 2: row starts */
+  int64_t* start = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+  if (!start) { free(cnt); return NULL; }
+  start[0] = 0;
+  for (int32_t u = 0; u < n; ++u) start[u + 1] = start[u] + cnt[u];
+  int64_t total = start[n];
+  int32_t* raw = (int32_t*)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
+  if (!raw) { free(cnt); free(start); return NULL; }
+  /* step 3: place u->v and v->u */
+  for (int32_t u = 0; u < n; ++u) cnt[u] = start[u];
+  for (int64_t e = 0; e < m; ++e) {
+    int32_t u = src[e], v = dst[e];
+    if (u == v) continue;
+    raw[cnt[u]++] = v;
+    raw[cnt[v]++] = u;
+  }
+  /* step 4: sort each row, keep each neighbour once */
+  int64_t* off = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
+  if (!off) { free(cnt); free(start); free(raw); return NULL; }
+  int64_t w = 0;
+  off[0] = 0;
+  for (int32_t u = 0; u < n; ++u) {
+    int64_t b = start[u], e = start[u + 1];
+    if (e > b) qsort(raw + b, (size_t)(e - b), sizeof(int32_t), cmp_i32);
+    for (int64_t i = b; i < e; ++i) {
+      if (i > b && raw[i] == raw[i - 1]) continue;
+      raw[w++] = raw[i];
+    }
+    off[u + 1] = w;
+  }
+  free(cnt);
+  free(start);
+  orc_graph* g = (orc_graph*)malloc(sizeof(orc_graph));
+  if (!g) { free(raw); free(off); return NULL; }
+  g->n = n;
+  g->nnz = w;
+  g->off = off;
+  g->col = (int32_t*)realloc(raw, (size_t)(w > 0 ? w : 1) * sizeof(int32_t));
+  if (!g->col) g->col = raw;
+  return g;
+}
+
+void orc_graph_free(orc_graph* g) {
+  if (!g) return;
+  free(g->off);
+  free(g->col);
+  free(g);
+}
+
+int32_t orc_graph_n(const orc_graph* g) { return g->n; }
+int64_t orc_graph_nnz(const orc_graph* g) { return g->nnz; }
+
+void orc_graph_copy(const orc_graph* g, int64_t* off, int32_t* col) {
+  memcpy(off, g->off, ((size_t)g->n + 1) * sizeof(int64_t));
+  if (g->nnz > 0) memcpy(col, g->col, (size_t)g->nnz * sizeof(int32_t));
+}
+
+/* Hop distance (Sec. VI-A.3: the output is the hop distance from the source),
+ * by the textbook FIFO-queue BFS. */
+static int bfs_depth(const orc_graph* g, int32_t s, int32_t* depth) {
+  int32_t n = g->n;
+  int32_t* queue = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  if (!queue) return ORC_ERR_OOM;
+  for (int32_t v = 0; v < n; ++v) depth[v] = -1;
+  int64_t head = 0, tail = 0;
+  depth[s] = 0;
+  queue[tail++] = s;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (int64_t i = g->off[u]; i < g->off[u + 1]; ++i) {
+      int32_t v = g->col[i];
+      if (depth[v] == -1) {
+        depth[v] = depth[u] + 1;
+        queue[tail++] = v;
+      }
+    }
+  }
+  free(queue);
+  return ORC_OK;
+}
+
+/* Canonical BFS-tree parent: the smallest-id neighbour one level closer to the
+ * source.  Computed as an explicit minimum over the whole row, so it does not
+ * rely on the rows being sorted. */
+static void canonical_parent(const orc_graph* g, int32_t s, const int32_t* depth, int32_t* parent) {
+  for (int32_t v = 0; v < g->n; ++v) {
+    parent[v] = -1;
+    if (v == s) { parent[v] = s; continue; }
+    if (depth[v] <= 0) continue;
+    int32_t best = -1;
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      int32_t u = g->col[i];
+      if (depth[u] == depth[v] - 1 && (best == -1 || u < best)) best = u;
+    }
+    parent[v] = best;
+  }
+}
+
+int orc_bfs(const orc_graph* g, int32_t s, int32_t* depth, int32_t* parent) {
+  if (!g || !depth || !parent || s < 0 || s >= g->n) return ORC_ERR_INVALID;
+  int rc = bfs_depth(g, s, depth);
+  if (rc) return rc;
+  canonical_parent(g, s, depth, parent);
+  return ORC_OK;
+}
+
+int orc_bfs_batch_u8(const orc_graph* g, int32_t k, const int32_t* sources, uint8_t* depth,
+                     int32_t* parent) {
+  if (!g || k < 0 || (k > 0 && (!sources || !depth || !parent))) return ORC_ERR_INVALID;
+  int32_t n = g->n;
+  for (int32_t j = 0; j < k; ++j)
+    if (sources[j] < 0 || sources[j] >= n) return ORC_ERR_INVALID;
+  int32_t* d32 = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  if (!d32) return ORC_ERR_OOM;
+  int overflow = 0;
+  for (int32_t j = 0; j < k; ++j) {
+    int rc = orc_bfs(g, sources[j], d32, parent + (size_t)j * n);
+    if (rc) { free(d32); return rc; }
+    for (int32_t v = 0; v < n; ++v) {
+      int32_t dv = d32[v];
+      if (dv > 254) overflow = 1;
+      depth[(size_t)j * n + v] = (uint8_t)(dv < 0 ? 255 : (dv > 254 ? 254 : dv));
+    }
+  }
+  free(d32);
+  return overflow ? ORC_ERR_OVERFLOW : ORC_OK;
+}
+
+int64_t orc_component_edges(const orc_graph* g, const int32_t* depth) {
+  int64_t ends = 0;
+  for (int32_t v = 0; v < g->n; ++v) {
+    if (depth[v] < 0) continue;
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i)
+      if (depth[g->col[i]] >= 0) ends += 1;
+  }
+  return ends / 2; /* every undirected edge is stored twice */
+}
+
+static int is_edge(const orc_graph* g, int32_t u, int32_t v) {
+  for (int64_t i = g->off[u]; i < g->off[u + 1]; ++i)
+    if (g->col[i] == v) return 1;
+  return 0;
+}
+
+static int32_t uf_find(int32_t* p, int32_t x) {
+  while (p[x] != x) {
+    p[x] = p[p[x]];
+    x = p[x];
+  }
+  return x;
+}
+
+int orc_validate(const orc_graph* g, int32_t s, const int32_t* depth, const int32_t* parent) {
+  int32_t n = g->n;
+  if (s < 0 || s >= n) return 9;
+  for (int32_t v = 0; v < n; ++v) {
+    if (depth[v] < -1 || depth[v] >= n) return 9;
+    if (parent[v] < -1 || parent[v] >= n) return 9;
+  }
+  if (depth[s] != 0 || parent[s] != s) return 1;
+  for (int32_t u = 0; u < n; ++u) {
+    for (int64_t i = g->off[u]; i < g->off[u + 1]; ++i) {
+      int32_t v = g->col[i];
+      if ((depth[u] >= 0) != (depth[v] >= 0)) return 2;
+      if (depth[u] >= 0) {
+        int32_t diff = depth[u] - depth[v];
+        if (diff > 1 || diff < -1) return 3;
+      }
+    }
+  }
+  for (int32_t v = 0; v < n; ++v) {
+    if (v == s) continue;
+    if (depth[v] < 0) {
+      if (parent[v] != -1) return 7;
+      continue;
+    }
+    int32_t p = parent[v];
+    if (p < 0 || !is_edge(g, p, v)) return 4;
+    if (depth[p] != depth[v] - 1) return 5;
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      int32_t u = g->col[i];
+      if (u < p && depth[u] == depth[v] - 1) return 6;
+    }
+  }
+  /* reached set == connected component of s, by union-find over all edges */
+  int32_t* uf = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  if (!uf) return ORC_ERR_OOM;
+  for (int32_t v = 0; v < n; ++v) uf[v] = v;
+  for (int32_t u = 0; u < n; ++u)
+    for (int64_t i = g->off[u]; i < g->off[u + 1]; ++i) {
+      int32_t a = uf_find(uf, u), b = uf_find(uf, g->col[i]);
+      if (a != b) uf[a] = b;
+    }
+  int32_t rs = uf_find(uf, s);
+  int bad = 0;
+  for (int32_t v = 0; v < n && !bad; ++v)
+    if ((uf_find(uf, v) == rs) != (depth[v] >= 0)) bad = 1;
+  free(uf);
+  return bad ? 8 : 0;
+}
+
+/* Sec. III-A: delegates are the vertices with more than TH neighbours, normal
+ * vertices the rest; Fig. 2 renumbers delegates in ascending original id.  The
+ * device layout places the non-isolated normal vertices next and the isolated
+ * ones last, each class in ascending original id. */
+void orc_separate(const orc_graph* g, int64_t th, int32_t* internal_of, int32_t* caller_of,
+                  int32_t* d_out, int32_t* n_ni_out) {
+  int32_t n = g->n;
+  int32_t next = 0;
+  for (int32_t v = 0; v < n; ++v) /* class 0: delegates */
+    if (g->off[v + 1] - g->off[v] > th) internal_of[v] = next++;
+  int32_t d = next;
+  for (int32_t v = 0; v < n; ++v) { /* class 1: normal vertices with a neighbour */
+    int64_t deg = g->off[v + 1] - g->off[v];
+    if (deg > 0 && deg <= th) internal_of[v] = next++;
+  }
+  int32_t n_ni = next;
+  for (int32_t v = 0; v < n; ++v) { /* class 2: isolated vertices */
+    int64_t deg = g->off[v + 1] - g->off[v];
+    if (deg == 0 && deg <= th) internal_of[v] = next++;
+  }
+  for (int32_t v = 0; v < n; ++v) caller_of[internal_of[v]] = v;
+  *d_out = d;
+  *n_ni_out = n_ni;
+}
+
+/* Sec. IV: nn, nd, dn and dd are the edges from normal/delegate sources to
+ * normal/delegate destinations. */
+void orc_subgraph_counts(const orc_graph* g, int64_t th, int64_t counts[4]) {
+  counts[0] = counts[1] = counts[2] = counts[3] = 0;
+  for (int32_t u = 0; u < g->n; ++u) {
+    int u_del = (g->off[u + 1] - g->off[u]) > th;
+    for (int64_t i = g->off[u]; i < g->off[u + 1]; ++i) {
+      int32_t v = g->col[i];
+      int v_del = (g->off[v + 1] - g->off[v]) > th;
+      counts[(u_del << 1) | v_del] += 1;
+    }
+  }
+}

@@ -1,0 +1,91 @@
+/*
+ * CPU oracle for single-GPU direction-optimized BFS over a degree-separated graph.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the package smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The GPU product path
+ * never links, loads or calls it, and it shares no code with the GPU path.
+ *
+ * Everything here is the plain definition of the result, written for a reader
+ * to check against the paper by eye (Pan, Pearce, Owens, "Scalable Breadth-First
+ * Search on a GPU Cluster", arXiv 1803.03922):
+ *   - the graph is symmetric: every undirected edge is stored in both directions
+ *     (Sec. II-B "Terminology"; Sec. VI-A.3 "edge doubling");
+ *   - delegates are vertices whose out-degree is larger than TH, normal vertices
+ *     the rest (Sec. II-B; Sec. III-A), renumbered to delegate ids in ascending
+ *     original id (Fig. 2: vertices 7 and 8 become delegates 0 and 1);
+ *   - the BFS output is the hop distance from the source (Sec. VI-A.3), plus a
+ *     canonical BFS-tree parent (smallest-id neighbour one level closer to the
+ *     source), the tree the paper discusses in Sec. VI-A.3 but does not build;
+ *   - direction optimization changes only which edges are examined, never the
+ *     output (Sec. IV-B), so one queue BFS defines the result of every schedule.
+ *
+ * All ids are the caller's ids.  Offsets are int64, columns int32.
+ * Functions returning int return 0 on success and a negative code on error.
+ */
+#ifndef BFS_ORACLE_H
+#define BFS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_graph orc_graph;
+
+/* Error codes. */
+#define ORC_OK 0
+#define ORC_ERR_INVALID (-1)
+#define ORC_ERR_OOM (-2)
+#define ORC_ERR_OVERFLOW (-3)
+
+/* Symmetric simple graph from an edge list (Sec. II-B; Sec. VI-A.3): self-loops
+ * are dropped, each remaining pair (u,v) is stored as u->v and v->u, and each
+ * row holds its neighbours once, in ascending id.  Returns NULL on bad input
+ * (n <= 0, m < 0, an id outside [0,n)) or when memory runs out. */
+orc_graph* orc_graph_build(int32_t n, int64_t m, const int32_t* src, const int32_t* dst);
+void orc_graph_free(orc_graph* g);
+int32_t orc_graph_n(const orc_graph* g);
+int64_t orc_graph_nnz(const orc_graph* g); /* directed entries = 2 x unique undirected edges */
+/* Copies the row offsets (n+1 entries) and the columns (nnz entries). */
+void orc_graph_copy(const orc_graph* g, int64_t* off, int32_t* col);
+
+/* Hop distance by a FIFO-queue BFS, then the canonical parent by a separate pass:
+ * parent[v] = min{u in N(v) : depth[u] = depth[v]-1}; parent[s] = s; unreached
+ * vertices get depth -1 and parent -1 (Sec. VI-A.3). */
+int orc_bfs(const orc_graph* g, int32_t s, int32_t* depth, int32_t* parent);
+
+/* Same computation for k sources, with uint8 depth (255 = unreached) laid out
+ * [k][n]; parent int32 [k][n].  ORC_ERR_OVERFLOW if some depth exceeds 254. */
+int orc_bfs_batch_u8(const orc_graph* g, int32_t k, const int32_t* sources, uint8_t* depth,
+                     int32_t* parent);
+
+/* Unique undirected edges whose endpoints are both reached (the traversed
+ * component's edge count, used as the numerator of GTEPS). */
+int64_t orc_component_edges(const orc_graph* g, const int32_t* depth);
+
+/* Graph500-style check of a (depth, parent) pair.  Returns 0 when every rule
+ * holds, otherwise a positive rule number:
+ *  1 depth[s] != 0 or parent[s] != s      2 an edge joins a reached and an unreached vertex
+ *  3 |depth(u)-depth(v)| > 1 on an edge    4 (parent[v], v) is not an edge
+ *  5 depth[parent[v]] != depth[v]-1        6 a smaller-id neighbour sits at depth[v]-1
+ *  7 unreached vertex with parent != -1    8 reached set != union-find component of s
+ *  9 depth/parent out of range */
+int orc_validate(const orc_graph* g, int32_t s, const int32_t* depth, const int32_t* parent);
+
+/* Degree separation (Sec. III-A) and the id layout it implies for the device
+ * graph: delegates (degree > th) take ids [0,d) in ascending original id (Fig. 2),
+ * non-isolated normal vertices take [d, n_ni) in ascending original id, and
+ * isolated vertices (degree 0) take [n_ni, n) in ascending original id.
+ * internal_of[caller] and caller_of[internal] are filled (n entries each). */
+void orc_separate(const orc_graph* g, int64_t th, int32_t* internal_of, int32_t* caller_of,
+                  int32_t* d, int32_t* n_ni);
+
+/* Directed entry counts of the four subgraphs of Sec. IV (nn, nd, dn, dd) for a
+ * threshold th: counts[0]=|E_nn|, counts[1]=|E_nd|, counts[2]=|E_dn|, counts[3]=|E_dd|. */
+void orc_subgraph_counts(const orc_graph* g, int64_t th, int64_t counts[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,397 @@
+"""Pins for the CPU oracle: checks against what the mathematics fixes, written
+independently of ``oracle.c`` (closed forms, shortest-path enumeration,
+library routines, invariants).  ``run_all(lib)`` runs every pin against a given
+build of the oracle and returns the names of the pins that failed, so a test
+can also show that a deliberately broken oracle is caught.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+import oracle
+
+
+def _g(n, edges, lib):
+    if len(edges):
+        e = np.asarray(edges, dtype=np.int32)
+        return oracle.Graph(n, e[:, 0], e[:, 1], lib=lib)
+    return oracle.Graph(n, np.zeros(0, np.int32), np.zeros(0, np.int32), lib=lib)
+
+
+# ---- closed forms -------------------------------------------------------------------------
+
+def pin_path_end(lib):
+    n = 37
+    g = _g(n, [(i, i + 1) for i in range(n - 1)], lib)
+    d, p = g.bfs(0)
+    return (d == np.arange(n)).all() and p[0] == 0 and (p[1:] == np.arange(n - 1)).all()
+
+
+def pin_path_middle(lib):
+    n, s = 41, 17
+    g = _g(n, [(i + 1, i) for i in range(n - 1)], lib)
+    d, p = g.bfs(s)
+    want_d = np.abs(np.arange(n) - s)
+    want_p = np.where(np.arange(n) < s, np.arange(n) + 1, np.arange(n) - 1)
+    want_p[s] = s
+    return (d == want_d).all() and (p == want_p).all()
+
+
+def pin_star(lib):
+    n, c = 50, 13
+    g = _g(n, [(c, v) for v in range(n) if v != c], lib)
+    d, p = g.bfs(c)
+    ok = d[c] == 0 and (np.delete(d, c) == 1).all() and (np.delete(p, c) == c).all() and p[c] == c
+    leaf = 40
+    d, p = g.bfs(leaf)
+    want = np.full(n, 2)
+    want[c], want[leaf] = 1, 0
+    wp = np.full(n, c)
+    wp[leaf] = leaf
+    wp[c] = leaf
+    return ok and (d == want).all() and (p == wp).all()
+
+
+def pin_grid(lib):
+    R, C = 9, 13
+    ids = lambda r, c: r * C + c  # noqa: E731
+    e = []
+    for r in range(R):
+        for c in range(C):
+            if r + 1 < R:
+                e.append((ids(r, c), ids(r + 1, c)))
+            if c + 1 < C:
+                e.append((ids(r, c + 1), ids(r, c)))
+    g = _g(R * C, e, lib)
+    d, p = g.bfs(0)
+    for r in range(R):
+        for c in range(C):
+            v = ids(r, c)
+            if d[v] != r + c:
+                return False
+            if v == 0:
+                if p[v] != 0:
+                    return False
+                continue
+            # the up-neighbour has the smaller row-major id whenever it exists
+            want = ids(r - 1, c) if r > 0 else ids(r, c - 1)
+            if p[v] != want:
+                return False
+    return True
+
+
+def pin_binary_tree(lib):
+    n = 255
+    g = _g(n, [((i - 1) // 2, i) for i in range(1, n)], lib)
+    d, p = g.bfs(0)
+    i = np.arange(n)
+    want_d = np.floor(np.log2(i + 1)).astype(np.int64)
+    want_p = (i - 1) // 2
+    want_p[0] = 0
+    return (d == want_d).all() and (p == want_p).all()
+
+
+def pin_complete(lib):
+    n, s = 12, 5
+    g = _g(n, list(itertools.combinations(range(n), 2)), lib)
+    d, p = g.bfs(s)
+    want_d = np.ones(n)
+    want_d[s] = 0
+    return (d == want_d).all() and (p == s).all() and g.nnz == n * (n - 1)
+
+
+def pin_even_cycle(lib):
+    n = 20
+    g = _g(n, [(i, (i + 1) % n) for i in range(n)], lib)
+    d, p = g.bfs(0)
+    i = np.arange(n)
+    want_d = np.minimum(i, n - i)
+    want_p = np.where(i < n // 2, i - 1, (i + 1) % n)
+    want_p[0] = 0
+    want_p[n // 2] = n // 2 - 1  # antipode: two parents at the same depth, the smaller wins
+    return (d == want_d).all() and (p == want_p).all()
+
+
+def pin_components_and_isolated(lib):
+    # two paths and an isolated vertex; source in the second path
+    e = [(0, 1), (1, 2), (4, 5), (5, 6), (6, 7)]
+    g = _g(9, e, lib)
+    d, p = g.bfs(5)
+    ok = list(d) == [-1, -1, -1, -1, 1, 0, 1, 2, -1] and list(p) == [-1, -1, -1, -1, 5, 5, 5, 6, -1]
+    d, p = g.bfs(8)  # isolated source
+    want = [-1] * 9
+    want[8] = 0
+    wp = [-1] * 9
+    wp[8] = 8
+    return ok and list(d) == want and list(p) == wp
+
+
+def pin_dedup_selfloops(lib):
+    e = [(0, 1), (1, 0), (0, 1), (2, 2), (1, 2), (2, 1), (3, 3)]
+    g = _g(4, e, lib)
+    off, col = g.csr()
+    return list(off) == [0, 1, 3, 4, 4] and list(col) == [1, 0, 2, 1] and g.nnz == 4
+
+
+# ---- brute force --------------------------------------------------------------------------
+
+def _shortest_paths_enum(n, adj, s):
+    """All simple paths from s, kept when shortest; returns (dist, min penultimate)."""
+    dist = [-1] * n
+    pen = [-1] * n
+    dist[s] = 0
+    pen[s] = s
+    stack = [(s, (s,))]
+    paths = {}
+    while stack:
+        v, path = stack.pop()
+        for u in range(n):
+            if adj[v][u] and u not in path:
+                L = len(path)
+                paths.setdefault(u, []).append((L, v))
+                stack.append((u, path + (u,)))
+    for u, lst in paths.items():
+        L = min(x for x, _ in lst)
+        dist[u] = L
+        pen[u] = min(v for x, v in lst if x == L)
+    return dist, pen
+
+
+def pin_exhaustive_5(lib):
+    n = 5
+    pairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(pairs)):
+        e = [pairs[i] for i in range(len(pairs)) if mask >> i & 1]
+        adj = [[0] * n for _ in range(n)]
+        for a, b in e:
+            adj[a][b] = adj[b][a] = 1
+        g = _g(n, e, lib)
+        for s in range(n):
+            d, p = g.bfs(s)
+            wd, wp = _shortest_paths_enum(n, adj, s)
+            if list(d) != wd or list(p) != wp:
+                return False
+    return True
+
+
+def pin_random_small_floyd(lib, trials=300, seed=1):
+    rng = np.random.default_rng(seed)
+    for _ in range(trials):
+        n = int(rng.integers(1, 11))
+        m = int(rng.integers(0, 3 * n))
+        src = rng.integers(0, n, m)
+        dst = rng.integers(0, n, m)
+        g = oracle.Graph(n, src, dst, lib=lib)
+        A = np.zeros((n, n), dtype=bool)
+        A[src, dst] = True
+        A[dst, src] = True
+        np.fill_diagonal(A, False)
+        INF = 10**9
+        D = np.where(A, 1, INF)
+        np.fill_diagonal(D, 0)
+        for k in range(n):  # Floyd-Warshall relaxation
+            D = np.minimum(D, D[:, k:k + 1] + D[k:k + 1, :])
+        s = int(rng.integers(0, n))
+        d, p = g.bfs(s)
+        want_d = np.where(D[s] >= INF, -1, D[s])
+        if not (d == want_d).all():
+            return False
+        adjl = A.astype(int).tolist()
+        if n <= 8:
+            _, wp = _shortest_paths_enum(n, adjl, s)
+            if list(p) != wp:
+                return False
+    return True
+
+
+# ---- library routines and invariants ------------------------------------------------------
+
+def _random_graph(rng, n, m):
+    return rng.integers(0, n, m).astype(np.int32), rng.integers(0, n, m).astype(np.int32)
+
+
+def pin_scipy_depth_components(lib, seed=7):
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components, shortest_path
+
+    rng = np.random.default_rng(seed)
+    n, m = 700, 900  # sparse: several components
+    src, dst = _random_graph(rng, n, m)
+    g = oracle.Graph(n, src, dst, lib=lib)
+    A = sp.coo_matrix((np.ones(m), (src, dst)), shape=(n, n)).tocsr()
+    A = ((A + A.T) > 0).astype(np.int8)
+    A.setdiag(0)
+    A.eliminate_zeros()
+    _, lab = connected_components(A, directed=False)
+    for s in rng.integers(0, n, 6):
+        d, p = g.bfs(int(s))
+        ref = shortest_path(A, method="D", unweighted=True, indices=int(s))
+        want = np.where(np.isinf(ref), -1, ref).astype(np.int64)
+        if not (d == want).all():
+            return False
+        if not ((d >= 0) == (lab == lab[s])).all():
+            return False
+    return True
+
+
+def pin_invariants_python(lib, seed=11):
+    """Graph500-style rules checked by code independent of the oracle's validator."""
+    rng = np.random.default_rng(seed)
+    n, m = 400, 1500
+    src, dst = _random_graph(rng, n, m)
+    g = oracle.Graph(n, src, dst, lib=lib)
+    off, col = g.csr()
+    for s in rng.integers(0, n, 5):
+        s = int(s)
+        d, p = g.bfs(s)
+        if d[s] != 0 or p[s] != s:
+            return False
+        for u in range(n):
+            nb = col[off[u]:off[u + 1]]
+            if ((d[u] >= 0) != (d[nb] >= 0)).any():
+                return False
+            if d[u] >= 0 and (np.abs(d[u] - d[nb]) > 1).any():
+                return False
+            if u == s:
+                continue
+            if d[u] < 0:
+                if p[u] != -1:
+                    return False
+                continue
+            cands = nb[d[nb] == d[u] - 1]
+            if p[u] not in set(nb.tolist()) or p[u] != cands.min():
+                return False
+    return True
+
+
+def pin_validator_detects(lib):
+    """The validator accepts the oracle's own answer and rejects planted faults."""
+    e = [(0, 1), (0, 2), (1, 3), (2, 3), (3, 4), (5, 6)]
+    g = _g(7, e, lib)
+    d, p = g.bfs(0)
+    if g.validate(0, d, p) != 0:
+        return False
+    checks = []
+    p2 = p.copy(); p2[3] = 2; checks.append((d, p2, 6))          # non-canonical parent
+    p2 = p.copy(); p2[4] = 0; checks.append((d, p2, 4))          # parent is not a neighbour
+    d2 = d.copy(); d2[4] = 5; checks.append((d2, p, 3))          # depth jump on an edge
+    d2 = d.copy(); d2[4] = -1; p2 = p.copy(); p2[4] = -1; checks.append((d2, p2, 2))
+    d2 = d.copy(); d2[0] = 1; checks.append((d2, p, 1))
+    p2 = p.copy(); p2[5] = 6; checks.append((d, p2, 7))
+    return all(g.validate(0, a, b) == want for a, b, want in checks)
+
+
+def pin_component_edges(lib, seed=3):
+    rng = np.random.default_rng(seed)
+    n, m = 300, 500
+    src, dst = _random_graph(rng, n, m)
+    g = oracle.Graph(n, src, dst, lib=lib)
+    s = int(src[0])
+    d, _ = g.bfs(s)
+    pairs = {(min(a, b), max(a, b)) for a, b in zip(src.tolist(), dst.tolist()) if a != b}
+    want = sum(1 for a, b in pairs if d[a] >= 0)
+    return g.component_edges(d) == want
+
+
+def pin_builder_sets(lib, seed=5):
+    rng = np.random.default_rng(seed)
+    for n, m in [(1, 3), (17, 60), (200, 3000)]:
+        src, dst = _random_graph(rng, n, m)
+        g = oracle.Graph(n, src, dst, lib=lib)
+        off, col = g.csr()
+        rows = [set() for _ in range(n)]
+        for a, b in zip(src.tolist(), dst.tolist()):
+            if a != b:
+                rows[a].add(b)
+                rows[b].add(a)
+        for u in range(n):
+            if col[off[u]:off[u + 1]].tolist() != sorted(rows[u]):
+                return False
+    return True
+
+
+def pin_separation(lib, seed=9):
+    """Sec. III-A: delegate iff degree > TH, delegate ids ascending (Fig. 2), then
+    non-isolated normal vertices, then isolated ones, each ascending."""
+    rng = np.random.default_rng(seed)
+    n, m = 500, 2500
+    src, dst = _random_graph(rng, n, m)
+    src[:40] = 3  # a hub
+    g = oracle.Graph(n, src, dst, lib=lib)
+    deg = g.degree()
+    for th in [-1, 0, 5, int(np.median(deg)), int(deg.max()) - 1, int(deg.max())]:
+        io, co, d, n_ni = g.separate(th)
+        dl = np.flatnonzero(deg > th)
+        nl = np.flatnonzero((deg > 0) & (deg <= th))
+        il = np.flatnonzero((deg == 0) & (deg <= th))
+        if th < 0:
+            nl = np.zeros(0, dtype=np.int64)
+            il = np.zeros(0, dtype=np.int64)
+        order = np.concatenate([dl, nl, il])
+        if d != dl.size or n_ni != dl.size + nl.size:
+            return False
+        if not (co == order).all() or not (io[order] == np.arange(n)).all():
+            return False
+    return True
+
+
+def pin_subgraph_counts(lib, seed=13):
+    rng = np.random.default_rng(seed)
+    n, m = 300, 2000
+    src, dst = _random_graph(rng, n, m)
+    src[:50] = 7
+    g = oracle.Graph(n, src, dst, lib=lib)
+    off, col = g.csr()
+    deg = np.diff(off)
+    for th in [0, 4, 8, 16, 10**9]:
+        got = g.subgraph_counts(th)
+        want = np.zeros(4, dtype=np.int64)
+        for u in range(n):
+            for v in col[off[u]:off[u + 1]]:
+                want[2 * int(deg[u] > th) + int(deg[v] > th)] += 1
+        if not (got == want).all() or got.sum() != g.nnz or got[1] != got[2]:
+            return False
+    return True
+
+
+def pin_batch_u8(lib):
+    e = [(i, i + 1) for i in range(30)] + [(40, 41)]
+    g = _g(50, e, lib)
+    srcs = [0, 15, 40, 45]
+    D, P = g.bfs_batch_u8(srcs)
+    for j, s in enumerate(srcs):
+        d, p = g.bfs(s)
+        if not (D[j] == np.where(d < 0, 255, d)).all() or not (P[j] == p).all():
+            return False
+    # a path of 300 vertices from an end reaches depth 299 > 254
+    g2 = _g(300, [(i, i + 1) for i in range(299)], lib)
+    try:
+        g2.bfs_batch_u8([0])
+        return False
+    except OverflowError:
+        pass
+    D, _ = g2.bfs_batch_u8([150])  # depth <= 150 fits
+    return int(D.max()) == 150
+
+
+PINS = [
+    pin_path_end, pin_path_middle, pin_star, pin_grid, pin_binary_tree, pin_complete,
+    pin_even_cycle, pin_components_and_isolated, pin_dedup_selfloops, pin_exhaustive_5,
+    pin_random_small_floyd, pin_scipy_depth_components, pin_invariants_python,
+    pin_validator_detects, pin_component_edges, pin_builder_sets, pin_separation,
+    pin_subgraph_counts, pin_batch_u8,
+]
+
+
+def run_all(lib, pins=None):
+    failed = []
+    for pin in pins or PINS:
+        try:
+            ok = bool(pin(lib))
+        except Exception:  # a crash or a rejected call counts as a failed pin
+            ok = False
+        if not ok:
+            failed.append(pin.__name__)
+    return failed
