@@ -1,0 +1,178 @@
+/*
+ * bfs_gb300 — direction-optimized breadth-first search over a degree-separated
+ * graph on one NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes only.
+ *
+ * Method: Pan, Pearce, Owens, "Scalable Breadth-First Search on a GPU Cluster"
+ * (arXiv 1803.03922), single-GPU part:
+ *   - degree separation: vertices with more than TH neighbours are delegates,
+ *     the rest normal vertices (Sec. II-B, Sec. III-A); delegates are renumbered
+ *     into a dense prefix of the id space in ascending original id (Fig. 2);
+ *   - compact storage: int32 column indices (Sec. III-C, Table I);
+ *   - per level, either a forward (top-down, push) visit with load balancing per
+ *     degree class (Sec. IV-A) or a backward (bottom-up, pull) visit that stops
+ *     at the first visited parent (Sec. II-C, Sec. IV-B), chosen per level by a
+ *     direction heuristic (Sec. IV-B; Beamer's alpha/beta rule by default);
+ *   - the output is the hop distance (Sec. VI-A.3) plus a canonical BFS-tree
+ *     parent (the smallest-id neighbour one level closer to the source).
+ *
+ * Ids in every argument and result are the caller's ids.
+ *
+ * Errors: every int-returning call returns BFS_OK (0) or a negative code; the
+ * message of the calling thread's last error is bfs_last_error().  On error the
+ * outputs are unspecified and a graph handle passed in stays valid.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ */
+#ifndef BFS_GB300_H
+#define BFS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is `struct CUstream_st*` */
+
+#define BFS_OK 0
+#define BFS_ERR_INVALID (-1)  /* null pointer, n <= 0, id or source out of range, bad option */
+#define BFS_ERR_OOM (-2)      /* device or host allocation failed */
+#define BFS_ERR_OVERFLOW (-3) /* a size beyond the int32/int64 layout, or a batched depth > 254 */
+#define BFS_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired; the context stays usable */
+#define BFS_ERR_CUDA (-5)     /* a CUDA runtime call failed */
+
+/* Direction schedules.  The output never depends on the schedule (Sec. IV-B:
+ * a visit direction changes only the work, not the input or the output). */
+#define BFS_SCHED_BEAMER 0    /* TD->BU when m_f*alpha > m_u; BU->TD when n_f*beta < n and shrinking */
+#define BFS_SCHED_TOPDOWN 1   /* every level forward (plain BFS) */
+#define BFS_SCHED_BOTTOMUP 2  /* level 0 forward, every later level backward */
+#define BFS_SCHED_ALTERNATE 3 /* even levels forward, odd levels backward */
+#define BFS_SCHED_MASK 4      /* level L backward iff bit min(L,63) of schedule_mask is set */
+#define BFS_SCHED_PAPER 5     /* Sec. IV-B workload rule: FV vs factor * BV, BV = |U|(q+s)/q */
+
+/* How a forward level picks the canonical parent of a newly reached vertex. */
+#define BFS_TD_PARENT_PULL 0      /* after the level, scan its sorted row for the first frontier neighbour */
+#define BFS_TD_PARENT_ATOMICMIN 1 /* atomicMin of the frontier neighbour's caller id during the visit */
+
+typedef struct bfs_options {
+  int64_t th;               /* degree threshold TH (>= 0): delegates have degree > th. Build-time. */
+  int32_t edges_on_device;  /* bfs_build_graph: 1 if src/dst are device pointers, 0 if host. */
+  int32_t schedule;         /* BFS_SCHED_* */
+  uint64_t schedule_mask;   /* for BFS_SCHED_MASK */
+  int32_t alpha;            /* Beamer alpha (default 15) */
+  int32_t beta;             /* Beamer beta (default 18) */
+  double factor0;           /* BFS_SCHED_PAPER: forward->backward when FV > factor0 * BV (default 0.5) */
+  double factor1;           /* BFS_SCHED_PAPER: backward->forward when FV < factor1 * BV (default 1e-7) */
+  int32_t td_parent;        /* BFS_TD_PARENT_* (default PULL) */
+  int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM (0 = as many as fit) */
+  int32_t barrier_timeout_ms; /* bound of every device-side grid-barrier wait (default 2000) */
+  int32_t test_skip_barrier;  /* testing only: CTA 0 leaves before the first grid barrier, so the
+                                 other CTAs' bounded wait expires and the run reports BFS_ERR_TIMEOUT */
+  int32_t run_timeout_ms;     /* bound of one run's device time (default 60000): BFS_ERR_TIMEOUT */
+  int32_t reserved[5];
+} bfs_options;
+
+/* Fills *opt with the defaults: th 64, host edges, Beamer alpha 15 / beta 18,
+ * paper factors 0.5 / 1e-7, PULL parents, 2000 ms barrier bound. */
+int bfs_options_default(bfs_options* opt);
+
+typedef struct bfs_graph bfs_graph;
+
+/* Builds the device graph (Sec. III; Table I layout with int64 row offsets):
+ * drops self-loops, stores every remaining pair in both directions (Sec. II-B),
+ * removes duplicates, sorts every row by the neighbour's caller id, separates
+ * delegates (degree > th) from normal vertices (Sec. III-A) and renumbers them:
+ * internal ids [0,d) are delegates in ascending caller id (Fig. 2), [d,n_ni)
+ * non-isolated normal vertices in ascending caller id, [n_ni,n) isolated ones.
+ *   src, dst      borrowed, read-only, num_edges int32 ids in [0, num_vertices);
+ *                 host memory, or device memory when opt->edges_on_device = 1.
+ *   num_vertices  1 .. 2^31-1.   num_edges >= 0 (2*num_edges entries must fit int64).
+ *   opt           NULL = defaults.
+ *   out           receives a handle owned by the library (release with bfs_free).
+ * Synchronizes `stream`.  Errors: INVALID (bad id, n, null), OOM, OVERFLOW, CUDA. */
+int bfs_build_graph(const int32_t* src, const int32_t* dst, int64_t num_edges, int32_t num_vertices,
+                    const bfs_options* opt, bfs_graph** out, struct CUstream_st* stream);
+
+/* Replaces the run-time options of a graph (everything but th and edges_on_device). */
+int bfs_set_options(bfs_graph* g, const bfs_options* opt);
+
+typedef struct bfs_graph_info {
+  int32_t n;              /* vertices */
+  int32_t n_nonisolated;  /* vertices with degree > 0 (= n_ni) */
+  int32_t delegates;      /* d: vertices with degree > th */
+  int32_t grid_blocks;    /* CTAs of the level-loop kernel */
+  int64_t th;
+  int64_t nnz;            /* directed entries = 2 x unique undirected non-loop edges */
+  int64_t max_degree;
+  int64_t subgraph_edges[4]; /* directed entries of nn, nd, dn, dd (Sec. IV) */
+  int64_t chunk_capacity; /* work-list entries reserved for delegate rows */
+  int64_t device_bytes;   /* device memory held by the graph */
+} bfs_graph_info;
+
+int bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* info);
+
+/* Copies the device graph to caller-owned HOST buffers (synchronous):
+ * row_off[n_ni+1] int64 and col[nnz] int32 in internal ids; caller_of[n]
+ * (internal -> caller) and internal_of[n] (caller -> internal).  Any pointer may
+ * be NULL to skip that array. */
+int bfs_graph_export(const bfs_graph* g, int64_t* row_off, int32_t* col, int32_t* caller_of,
+                     int32_t* internal_of);
+
+#define BFS_LOG_LEVELS 256
+
+/* One level of a run, as logged by the device. */
+typedef struct bfs_level_log {
+  int32_t direction;      /* 0 forward (top-down), 1 backward (bottom-up) */
+  int32_t converted;      /* 1 if the frontier bitmap was converted to queues first */
+  int64_t frontier;       /* |F_L|: vertices at depth L */
+  int64_t frontier_edges; /* m_f: sum of degrees over F_L */
+  int64_t scanned;        /* backward: unvisited non-isolated vertices scanned */
+  int64_t edges_examined; /* forward: m_f; backward: sum over scanned v of k_v */
+  int64_t parent_edges;   /* forward with PULL parents: row entries read to pick parents */
+  int64_t found;          /* |F_{L+1}| */
+  int64_t queue_entries;  /* normal-vertex queue entries holding F_L (forward levels) */
+  uint64_t t_begin_ns, t_expand_ns, t_end_ns; /* device %globaltimer at the phase edges */
+} bfs_level_log;
+
+typedef struct bfs_stats {
+  int32_t levels;          /* levels run (= max depth + 1) */
+  int32_t logged_levels;   /* min(levels, BFS_LOG_LEVELS) */
+  int64_t reached;         /* vertices with depth >= 0 */
+  int64_t component_edges; /* unique undirected edges in the traversed component (GTEPS numerator) */
+  int64_t edges_examined;  /* sum over levels */
+  int64_t model_bytes;     /* algorithmic HBM bytes of this run (byte model of the design notes) */
+  uint64_t device_ns;      /* %globaltimer span of the level loop */
+  bfs_level_log level[BFS_LOG_LEVELS];
+} bfs_stats;
+
+/* One BFS from `source` (a caller id).  depth[n] and parent[n] are caller-owned
+ * int32 buffers indexed by caller id, both in device memory or both in host
+ * memory: depth[v] = hop distance (-1 unreached), parent[v] = canonical parent
+ * (parent[source] = source, -1 unreached).  Device buffers: asynchronous on
+ * `stream`.  Host buffers: results are copied back and `stream` is synchronized.
+ * stats (optional, host): filled after synchronizing `stream`.
+ * One run at a time per graph: runs on one stream are ordered; runs of the same
+ * graph on different streams must not overlap.
+ * Errors: INVALID (null, source out of range), TIMEOUT, CUDA. */
+int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* parent, bfs_stats* stats,
+            struct CUstream_st* stream);
+
+/* Synchronizes `stream` and returns the device-side status of the graph's most
+ * recent run: BFS_OK, or BFS_ERR_TIMEOUT when a bounded wait expired (runs with
+ * device buffers and no stats do not report it themselves). */
+int bfs_wait(bfs_graph* g, struct CUstream_st* stream);
+
+/* Releases every device and host resource of the graph.  NULL is a no-op. */
+void bfs_free(bfs_graph* g);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* bfs_last_error(void);
+
+/* sizeof of the ABI structs, for bindings to check their layouts:
+ * sizes[0] bfs_options, [1] bfs_graph_info, [2] bfs_level_log, [3] bfs_stats. */
+void bfs_abi_sizes(int64_t sizes[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -64,6 +64,8 @@ def _bind(lib):
     lib.orc_separate.argtypes = [P, i64, P, P, P, P]
     lib.orc_subgraph_counts.restype = None
     lib.orc_subgraph_counts.argtypes = [P, i64, P]
+    lib.orc_level_counters.restype = ctypes.c_int
+    lib.orc_level_counters.argtypes = [P, i32, P, i64, i32, P, P]
     return lib
 
 
@@ -161,6 +163,16 @@ class Graph:
         self._lib.orc_separate(self._h, int(th), _ptr(internal_of), _ptr(caller_of),
                                ctypes.byref(d), ctypes.byref(n_ni))
         return internal_of, caller_of, int(d.value), int(n_ni.value)
+
+    def level_counters(self, s: int, depth, th: int, dirs):
+        """Per-level work counters [levels, 7] for the given directions (see oracle.h)."""
+        depth = np.ascontiguousarray(depth, dtype=np.int32)
+        dirs = np.ascontiguousarray(dirs, dtype=np.int32)
+        out = np.zeros((dirs.size, 7), dtype=np.int64)
+        rc = self._lib.orc_level_counters(self._h, int(s), _ptr(depth), int(th), dirs.size, _ptr(dirs), _ptr(out))
+        if rc:
+            raise ValueError("orc_level_counters failed with code %d" % rc)
+        return out
 
     def subgraph_counts(self, th: int):
         """Directed entry counts (|E_nn|, |E_nd|, |E_dn|, |E_dd|) for threshold th (Sec. IV)."""

@@ -277,3 +277,37 @@ void orc_subgraph_counts(const orc_graph* g, int64_t th, int64_t counts[4]) {
     }
   }
 }
+
+/* Position (1-based) of v's first neighbour at depth `level`, or its degree. */
+static int64_t first_hit(const orc_graph* g, const int32_t* depth, int32_t v, int32_t level) {
+  for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i)
+    if (depth[g->col[i]] == level) return i - g->off[v] + 1;
+  return g->off[v + 1] - g->off[v];
+}
+
+int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int64_t th, int32_t levels,
+                       const int32_t* dirs, int64_t* out) {
+  if (!g || !depth || !dirs || !out || levels < 0 || s < 0 || s >= g->n) return ORC_ERR_INVALID;
+  for (int32_t L = 0; L < levels; ++L) {
+    int64_t* o = out + (int64_t)L * 7;
+    for (int j = 0; j < 7; ++j) o[j] = 0;
+    for (int32_t v = 0; v < g->n; ++v) {
+      int64_t deg = g->off[v + 1] - g->off[v];
+      if (depth[v] == L) {
+        o[0] += 1;
+        o[1] += deg;
+        if (dirs[L] == 0 && deg > 0 && deg <= th) o[6] += 1;
+      }
+      if (depth[v] == L + 1) {
+        o[2] += 1;
+        if (dirs[L] == 0) o[5] += first_hit(g, depth, v, L);
+      }
+      int unvisited = depth[v] == -1 || depth[v] > L;
+      if (dirs[L] == 1 && unvisited && deg > 0) {
+        o[3] += 1;
+        o[4] += first_hit(g, depth, v, L);
+      }
+    }
+  }
+  return ORC_OK;
+}

@@ -85,6 +85,20 @@ void orc_separate(const orc_graph* g, int64_t th, int32_t* internal_of, int32_t*
  * threshold th: counts[0]=|E_nn|, counts[1]=|E_nd|, counts[2]=|E_dn|, counts[3]=|E_dd|. */
 void orc_subgraph_counts(const orc_graph* g, int64_t th, int64_t counts[4]);
 
+/* Per-level work counters of a direction-optimized run with the given per-level
+ * directions (dirs[L] = 0 forward, 1 backward), from the final depth of a run
+ * from s.  Rows are scanned in ascending neighbour id, so the position of the
+ * first visited neighbour is fixed (Sec. II-C: the backward visit stops at the
+ * first visited parent).  out[L*7 + j], j =
+ *  0 |F_L| (vertices at depth L)         1 m_f = sum of degrees over F_L
+ *  2 |F_{L+1}|
+ *  3 backward: unvisited vertices with a neighbour at the start of level L
+ *  4 backward: sum over those of k_v (first-hit position + 1, or the degree)
+ *  5 forward: sum over v in F_{L+1} of the first-hit position + 1 (parent pick)
+ *  6 forward: vertices of F_L with 0 < degree <= th (normal-vertex queue). */
+int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int64_t th, int32_t levels,
+                       const int32_t* dirs, int64_t* out);
+
 #ifdef __cplusplus
 }
 #endif

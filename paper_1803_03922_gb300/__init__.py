@@ -1,0 +1,275 @@
+"""Direction-optimized BFS over a degree-separated graph on one GB300 (sm_103a).
+
+Thin ctypes binding of the C ABI declared in ``include/bfs_gb300.h``: the
+functions below carry the same names and only marshal arguments (PyTorch tensors
+or numpy arrays to pointers, streams to ``cudaStream_t``).  Every step of the
+BFS runs in the CUDA kernels of ``libbfs_gb300.so``; there is no other path, and
+importing this package fails loudly when that library is missing.
+
+Method: Pan, Pearce, Owens, "Scalable Breadth-First Search on a GPU Cluster"
+(arXiv 1803.03922): degree separation (Sec. III-A), forward and backward visits
+(Sec. IV-A/B), direction optimization (Sec. IV-B), hop distance output
+(Sec. VI-A.3) plus a canonical BFS-tree parent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+BFS_OK = 0
+BFS_ERR_INVALID = -1
+BFS_ERR_OOM = -2
+BFS_ERR_OVERFLOW = -3
+BFS_ERR_TIMEOUT = -4
+BFS_ERR_CUDA = -5
+
+BFS_SCHED_BEAMER = 0
+BFS_SCHED_TOPDOWN = 1
+BFS_SCHED_BOTTOMUP = 2
+BFS_SCHED_ALTERNATE = 3
+BFS_SCHED_MASK = 4
+BFS_SCHED_PAPER = 5
+
+BFS_TD_PARENT_PULL = 0
+BFS_TD_PARENT_ATOMICMIN = 1
+
+BFS_LOG_LEVELS = 256
+
+c_i32, c_i64, c_u64, c_dbl, c_vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+
+
+class bfs_options(ctypes.Structure):
+    _fields_ = [("th", c_i64), ("edges_on_device", c_i32), ("schedule", c_i32), ("schedule_mask", c_u64),
+                ("alpha", c_i32), ("beta", c_i32), ("factor0", c_dbl), ("factor1", c_dbl),
+                ("td_parent", c_i32), ("blocks_per_sm", c_i32), ("barrier_timeout_ms", c_i32),
+                ("test_skip_barrier", c_i32), ("run_timeout_ms", c_i32), ("reserved", c_i32 * 5)]
+
+
+class bfs_graph_info(ctypes.Structure):
+    _fields_ = [("n", c_i32), ("n_nonisolated", c_i32), ("delegates", c_i32), ("grid_blocks", c_i32),
+                ("th", c_i64), ("nnz", c_i64), ("max_degree", c_i64), ("subgraph_edges", c_i64 * 4),
+                ("chunk_capacity", c_i64), ("device_bytes", c_i64)]
+
+
+class bfs_level_log(ctypes.Structure):
+    _fields_ = [("direction", c_i32), ("converted", c_i32), ("frontier", c_i64), ("frontier_edges", c_i64),
+                ("scanned", c_i64), ("edges_examined", c_i64), ("parent_edges", c_i64), ("found", c_i64),
+                ("queue_entries", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64)]
+
+
+class bfs_stats(ctypes.Structure):
+    _fields_ = [("levels", c_i32), ("logged_levels", c_i32), ("reached", c_i64), ("component_edges", c_i64),
+                ("edges_examined", c_i64), ("model_bytes", c_i64), ("device_ns", c_u64),
+                ("level", bfs_level_log * BFS_LOG_LEVELS)]
+
+
+class BfsError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__("bfs error %d: %s" % (code, message))
+        self.code = code
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libbfs_gb300.so is not built; run __graft_entry__.build() "
+                          "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(path)
+    lib.bfs_options_default.argtypes = [ctypes.POINTER(bfs_options)]
+    lib.bfs_build_graph.argtypes = [c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(bfs_options),
+                                    ctypes.POINTER(c_vp), c_vp]
+    lib.bfs_set_options.argtypes = [c_vp, ctypes.POINTER(bfs_options)]
+    lib.bfs_graph_get_info.argtypes = [c_vp, ctypes.POINTER(bfs_graph_info)]
+    lib.bfs_graph_export.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
+    lib.bfs_run.argtypes = [c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(bfs_stats), c_vp]
+    lib.bfs_wait.argtypes = [c_vp, c_vp]
+    lib.bfs_free.argtypes = [c_vp]
+    lib.bfs_free.restype = None
+    lib.bfs_last_error.restype = ctypes.c_char_p
+    lib.bfs_last_error.argtypes = []
+    lib.bfs_abi_sizes.argtypes = [ctypes.POINTER(c_i64 * 4)]
+    lib.bfs_abi_sizes.restype = None
+    sizes = (c_i64 * 4)()
+    lib.bfs_abi_sizes(ctypes.byref(sizes))
+    want = [ctypes.sizeof(t) for t in (bfs_options, bfs_graph_info, bfs_level_log, bfs_stats)]
+    if list(sizes) != want:
+        raise ImportError("ABI struct sizes differ: library %s, binding %s" % (list(sizes), want))
+    _lib = lib
+    return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(rc):
+    if rc != BFS_OK:
+        raise BfsError(rc, bfs_last_error())
+    return rc
+
+
+def _ptr(x):
+    """Pointer of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return c_vp(x.ctypes.data)
+    return c_vp(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        if not torch.cuda.is_available():
+            return None
+        return c_vp(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return c_vp(stream)
+    return c_vp(stream.cuda_stream)
+
+
+# ---- the C ABI, one function per entry point -------------------------------------------------
+
+def bfs_last_error() -> str:
+    return _load().bfs_last_error().decode()
+
+
+def bfs_options_default() -> bfs_options:
+    o = bfs_options()
+    _check(_load().bfs_options_default(ctypes.byref(o)))
+    return o
+
+
+def bfs_build_graph(src, dst, num_vertices: int, opt: bfs_options | None = None, stream=None):
+    """Returns an opaque handle.  src/dst: int32 CUDA tensors, or int32 host
+    arrays/tensors (``opt.edges_on_device`` is set from where they live)."""
+    lib = _load()
+    o = opt if opt is not None else bfs_options_default()
+    on_dev = not isinstance(src, np.ndarray) and getattr(src, "is_cuda", False)
+    o.edges_on_device = 1 if on_dev else 0
+    if isinstance(src, np.ndarray):
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        m = src.size
+    else:
+        if src.dtype != dst.dtype or str(src.dtype) != "torch.int32" or not src.is_contiguous() or \
+                not dst.is_contiguous():
+            raise ValueError("src and dst must be contiguous int32")
+        m = src.numel()
+    if (dst.size if isinstance(dst, np.ndarray) else dst.numel()) != m:
+        raise ValueError("src and dst differ in length")
+    h = c_vp()
+    _check(lib.bfs_build_graph(_ptr(src), _ptr(dst), m, int(num_vertices), ctypes.byref(o), ctypes.byref(h),
+                               _stream(stream)))
+    return h
+
+
+def bfs_set_options(g, opt: bfs_options):
+    _check(_load().bfs_set_options(g, ctypes.byref(opt)))
+
+
+def bfs_graph_get_info(g) -> bfs_graph_info:
+    info = bfs_graph_info()
+    _check(_load().bfs_graph_get_info(g, ctypes.byref(info)))
+    return info
+
+
+def bfs_graph_export(g):
+    """(row_off, col, caller_of, internal_of) as numpy arrays (internal ids)."""
+    info = bfs_graph_get_info(g)
+    off = np.empty(info.n_nonisolated + 1, dtype=np.int64)
+    col = np.empty(max(info.nnz, 1), dtype=np.int32)
+    co = np.empty(info.n, dtype=np.int32)
+    io = np.empty(info.n, dtype=np.int32)
+    _check(_load().bfs_graph_export(g, _ptr(off), _ptr(col), _ptr(co), _ptr(io)))
+    return off, col[: info.nnz], co, io
+
+
+def bfs_run(g, source: int, depth, parent, stats: bfs_stats | None = None, stream=None):
+    """depth/parent: int32 buffers of n entries, both CUDA tensors or both host
+    (numpy arrays / pinned tensors)."""
+    _check(_load().bfs_run(g, int(source), _ptr(depth), _ptr(parent),
+                           ctypes.byref(stats) if stats is not None else None, _stream(stream)))
+
+
+def bfs_wait(g, stream=None):
+    _check(_load().bfs_wait(g, _stream(stream)))
+
+
+def bfs_free(g):
+    if g:
+        _load().bfs_free(g)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------
+
+class Graph:
+    """A device-resident degree-separated graph and its BFS runs."""
+
+    def __init__(self, src, dst, num_vertices: int, th: int = 64, stream=None, **options):
+        opt = bfs_options_default()
+        opt.th = th
+        for k, v in options.items():
+            setattr(opt, k, v)
+        self._h = bfs_build_graph(src, dst, num_vertices, opt, stream)
+        self.info = bfs_graph_get_info(self._h)
+        self.n = self.info.n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_options(self, **options):
+        opt = bfs_options_default()
+        for k, v in options.items():
+            setattr(opt, k, v)
+        bfs_set_options(self._h, opt)
+
+    def export(self):
+        return bfs_graph_export(self._h)
+
+    def run(self, source: int, depth=None, parent=None, stats: bool = False, stream=None):
+        """BFS from ``source`` into CUDA tensors (allocated when not given).
+        Returns (depth, parent) or (depth, parent, bfs_stats)."""
+        import torch
+
+        if depth is None:
+            depth = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        if parent is None:
+            parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        st = bfs_stats() if stats else None
+        bfs_run(self._h, source, depth, parent, st, stream)
+        return (depth, parent, st) if stats else (depth, parent)
+
+    def wait(self, stream=None):
+        bfs_wait(self._h, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            bfs_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stats_to_dict(st: bfs_stats) -> dict:
+    out = {k: getattr(st, k) for k in ("levels", "logged_levels", "reached", "component_edges",
+                                       "edges_examined", "model_bytes", "device_ns")}
+    out["level"] = [{f: getattr(st.level[i], f) for f, _ in bfs_level_log._fields_}
+                    for i in range(st.logged_levels)]
+    return out

@@ -1,0 +1,343 @@
+// C ABI of the library: options, graph life cycle, runs, statistics, errors.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bfs_internal.cuh"
+
+namespace bfsgb {
+
+static thread_local std::string t_error;
+
+void set_error(const std::string& msg) { t_error = msg; }
+
+int fail(int code, const std::string& msg) {
+  t_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  t_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA;
+}
+
+int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, const bfs_options& opt,
+                bfs_graph* g, cudaStream_t s);
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      cudaSetDevice(dev);
+    } else {
+      prev = -1;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+int dmalloc(T** p, size_t count, int64_t* total, const char* what) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
+  *total += (int64_t)bytes;
+  return BFS_OK;
+}
+
+int check_options(const bfs_options& o) {
+  if (o.th < 0) return fail(BFS_ERR_INVALID, "th must be >= 0");
+  if (o.schedule < BFS_SCHED_BEAMER || o.schedule > BFS_SCHED_PAPER) return fail(BFS_ERR_INVALID, "unknown schedule");
+  if (o.alpha <= 0 || o.beta <= 0) return fail(BFS_ERR_INVALID, "alpha and beta must be > 0");
+  if (o.td_parent != BFS_TD_PARENT_PULL && o.td_parent != BFS_TD_PARENT_ATOMICMIN)
+    return fail(BFS_ERR_INVALID, "unknown td_parent");
+  if (o.blocks_per_sm < 0) return fail(BFS_ERR_INVALID, "blocks_per_sm must be >= 0");
+  if (o.barrier_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "barrier_timeout_ms must be > 0");
+  if (o.run_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "run_timeout_ms must be > 0");
+  if (!(o.factor0 >= 0) || !(o.factor1 >= 0)) return fail(BFS_ERR_INVALID, "factors must be >= 0");
+  return BFS_OK;
+}
+
+int alloc_run_state(bfs_graph* g) {
+  int64_t& t = g->device_bytes;
+  g->words = ((int64_t)g->n_ni + 31) / 32;
+  const size_t words = (size_t)g->words + 32;
+  int rc;
+  if ((rc = dmalloc(&g->V, words, &t, "alloc V"))) return rc;
+  if ((rc = dmalloc(&g->N0, words, &t, "alloc N"))) return rc;
+  if ((rc = dmalloc(&g->N1, words, &t, "alloc N"))) return rc;
+  if ((rc = dmalloc(&g->depth_i, (size_t)g->n_ni + 1, &t, "alloc depth"))) return rc;
+  if ((rc = dmalloc(&g->parent_i, (size_t)g->n_ni + 1, &t, "alloc parent"))) return rc;
+  if ((rc = dmalloc(&g->Q0, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
+  if ((rc = dmalloc(&g->Q1, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
+  if ((rc = dmalloc(&g->CL0, (size_t)g->cl_cap, &t, "alloc chunk list"))) return rc;
+  if ((rc = dmalloc(&g->CL1, (size_t)g->cl_cap, &t, "alloc chunk list"))) return rc;
+  if ((rc = dmalloc(&g->slot, (size_t)kSlots, &t, "alloc counters"))) return rc;
+  if ((rc = dmalloc(&g->log, (size_t)BFS_LOG_LEVELS, &t, "alloc log"))) return rc;
+  if ((rc = dmalloc(&g->hdr, 1, &t, "alloc header"))) return rc;
+  cudaError_t e = cudaMemset(g->hdr, 0, sizeof(RunHeader));
+  if (e != cudaSuccess) return cuda_fail(e, "memset header");
+  e = cudaMemset(g->slot, 0, sizeof(LevelSlot) * kSlots);
+  if (e != cudaSuccess) return cuda_fail(e, "memset counters");
+  return BFS_OK;
+}
+
+void free_all(bfs_graph* g) {
+  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->V, g->N0, g->N1, g->depth_i,
+                  g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->slot, g->log, g->hdr, g->out_scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Status of the most recent run (needs the stream to be synchronized).
+int run_status(bfs_graph* g, RunHeader* h) {
+  cudaError_t e = cudaMemcpy(h, g->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read run header");
+  if (h->err != 0 && (h->err >> 4) == (g->epoch & 0x0FFFFFFFu)) {
+    int code = -(int)(h->err & 0xFu);
+    if (code == BFS_ERR_TIMEOUT) return fail(code, "a device-side grid barrier wait passed its deadline");
+    return fail(code, "the level-loop kernel reported an error");
+  }
+  return BFS_OK;
+}
+
+}  // namespace
+
+// Algorithmic HBM bytes of one run, from the per-level counters (the byte model
+// of the design notes): forward level 20*|F| + 8*m_f + 12*found (+ 16*found +
+// 8*parent_edges with PULL parents); backward level words*4 + 8*scanned +
+// 8*edges + 12*found; every level end 4 bitmap passes; a conversion one bitmap
+// pass + 4 per queue entry; the run's set-up 3 bitmap clears (+ 4*n_ni for
+// atomicMin parents) and the result pass 12*n + 8*reached + words*4.
+int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st) {
+  const int64_t bm = g->words * 4;  // one pass over a bitmap
+  int64_t b = 3 * bm + 12 * (int64_t)g->n + 8 * st->reached + bm;
+  if (g->opt.td_parent == BFS_TD_PARENT_ATOMICMIN) b += 4 * (int64_t)g->n_ni;
+  for (int L = 0; L < st->logged_levels; ++L) {
+    const bfs_level_log& l = st->level[L];
+    if (l.converted) b += bm + 4 * l.queue_entries;
+    if (l.direction == 0) {
+      b += 20 * l.frontier + 8 * l.frontier_edges + 12 * l.found;
+      if (g->opt.td_parent == BFS_TD_PARENT_PULL) b += 16 * l.found + 8 * l.parent_edges;
+    } else {
+      b += bm + 8 * l.scanned + 8 * l.edges_examined + 12 * l.found;
+    }
+    b += 4 * bm;
+  }
+  return b;
+}
+
+}  // namespace bfsgb
+
+using namespace bfsgb;
+
+extern "C" int bfs_options_default(bfs_options* opt) {
+  if (!opt) return fail(BFS_ERR_INVALID, "opt is NULL");
+  std::memset(opt, 0, sizeof(*opt));
+  opt->th = 64;
+  opt->edges_on_device = 0;
+  opt->schedule = BFS_SCHED_BEAMER;
+  opt->schedule_mask = 0;
+  opt->alpha = 15;
+  opt->beta = 18;
+  opt->factor0 = 0.5;
+  opt->factor1 = 1e-7;
+  opt->td_parent = BFS_TD_PARENT_PULL;
+  opt->blocks_per_sm = 0;
+  opt->barrier_timeout_ms = 2000;
+  opt->run_timeout_ms = 60000;
+  return BFS_OK;
+}
+
+extern "C" int bfs_build_graph(const int32_t* src, const int32_t* dst, int64_t num_edges, int32_t num_vertices,
+                               const bfs_options* opt, bfs_graph** out, struct CUstream_st* stream) {
+  if (!out) return fail(BFS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (num_vertices <= 0) return fail(BFS_ERR_INVALID, "num_vertices must be >= 1");
+  if (num_edges < 0) return fail(BFS_ERR_INVALID, "num_edges must be >= 0");
+  if (num_edges > 0 && (!src || !dst)) return fail(BFS_ERR_INVALID, "src or dst is NULL");
+  bfs_options o;
+  bfs_options_default(&o);
+  if (opt) o = *opt;
+  int rc = check_options(o);
+  if (rc) return rc;
+  bfs_graph* g = new (std::nothrow) bfs_graph();
+  if (!g) return fail(BFS_ERR_OOM, "host allocation failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = build_graph(src, dst, num_edges, num_vertices, o, g, s);
+  if (!rc) rc = alloc_run_state(g);
+  if (!rc) rc = configure_run(g);
+  if (rc) {
+    std::string msg = bfs_last_error();
+    cudaStreamSynchronize(s);
+    free_all(g);
+    delete g;
+    set_error(msg);
+    return rc;
+  }
+  *out = g;
+  return BFS_OK;
+}
+
+extern "C" int bfs_set_options(bfs_graph* g, const bfs_options* opt) {
+  if (!g || !opt) return fail(BFS_ERR_INVALID, "graph or opt is NULL");
+  bfs_options o = *opt;
+  o.th = g->opt.th;
+  o.edges_on_device = g->opt.edges_on_device;
+  int rc = check_options(o);
+  if (rc) return rc;
+  const int old_bps = g->opt.blocks_per_sm;
+  g->opt = o;
+  if (o.blocks_per_sm != old_bps) {
+    DeviceGuard dg(g->device);
+    rc = configure_run(g);
+    if (rc) return rc;
+  }
+  return BFS_OK;
+}
+
+extern "C" int bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* info) {
+  if (!g || !info) return fail(BFS_ERR_INVALID, "graph or info is NULL");
+  std::memset(info, 0, sizeof(*info));
+  info->n = g->n;
+  info->n_nonisolated = g->n_ni;
+  info->delegates = g->d;
+  info->grid_blocks = g->grid_blocks;
+  info->th = g->th;
+  info->nnz = g->nnz;
+  info->max_degree = g->max_deg;
+  for (int j = 0; j < 4; ++j) info->subgraph_edges[j] = g->sub[j];
+  info->chunk_capacity = g->cl_cap;
+  info->device_bytes = g->device_bytes;
+  return BFS_OK;
+}
+
+extern "C" int bfs_graph_export(const bfs_graph* g, int64_t* row_off, int32_t* col, int32_t* caller_of,
+                                int32_t* internal_of) {
+  if (!g) return fail(BFS_ERR_INVALID, "graph is NULL");
+  DeviceGuard dg(g->device);
+  cudaError_t e = cudaSuccess;
+  if (row_off) e = cudaMemcpy(row_off, g->off, ((size_t)g->n_ni + 1) * 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && col && g->nnz > 0) e = cudaMemcpy(col, g->col, (size_t)g->nnz * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && caller_of) e = cudaMemcpy(caller_of, g->caller_of, (size_t)g->n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && internal_of)
+    e = cudaMemcpy(internal_of, g->internal_of, (size_t)g->n * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "export");
+  return BFS_OK;
+}
+
+static int fill_stats(bfs_graph* g, bfs_stats* st, const RunHeader& h) {
+  std::memset(st, 0, sizeof(*st));
+  st->levels = h.levels;
+  st->logged_levels = h.levels < BFS_LOG_LEVELS ? h.levels : BFS_LOG_LEVELS;
+  st->reached = (int64_t)h.reached;
+  st->component_edges = (int64_t)(h.reached_edges / 2);
+  st->device_ns = h.t1 - h.t0;
+  if (st->logged_levels > 0) {
+    LevelLogDev lg[BFS_LOG_LEVELS];
+    cudaError_t e = cudaMemcpy(lg, g->log, sizeof(LevelLogDev) * st->logged_levels, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read level log");
+    for (int L = 0; L < st->logged_levels; ++L) {
+      bfs_level_log& o = st->level[L];
+      o.direction = lg[L].dir;
+      o.converted = lg[L].converted;
+      o.frontier = (int64_t)lg[L].n_f;
+      o.frontier_edges = (int64_t)lg[L].m_f;
+      o.scanned = (int64_t)lg[L].scanned;
+      o.edges_examined = (int64_t)lg[L].edges;
+      o.parent_edges = (int64_t)lg[L].fix_edges;
+      o.found = (int64_t)lg[L].found;
+      o.queue_entries = (int64_t)lg[L].qn;
+      o.t_begin_ns = lg[L].t_begin;
+      o.t_expand_ns = lg[L].t_expand;
+      o.t_end_ns = lg[L].t_end;
+      st->edges_examined += o.edges_examined;
+    }
+  }
+  st->model_bytes = model_bytes_from_log(g, st);
+  return BFS_OK;
+}
+
+extern "C" int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* parent, bfs_stats* stats,
+                       struct CUstream_st* stream) {
+  if (!g) return fail(BFS_ERR_INVALID, "graph is NULL");
+  if (!depth || !parent) return fail(BFS_ERR_INVALID, "depth or parent is NULL");
+  if (source < 0 || source >= g->n) return fail(BFS_ERR_INVALID, "source out of range");
+  DeviceGuard dg(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dd = is_device_ptr(depth), dp = is_device_ptr(parent);
+  if (dd != dp) return fail(BFS_ERR_INVALID, "depth and parent must both be device or both be host memory");
+  int rc;
+  if (dd) {
+    rc = launch_run(g, source, depth, parent, s);
+    if (rc) return rc;
+  } else {
+    if (!g->out_scratch) {
+      cudaError_t e = cudaMalloc(&g->out_scratch, (size_t)g->n * 8);
+      if (e != cudaSuccess) {
+        g->out_scratch = nullptr;
+        return cuda_fail(e, "alloc output scratch");
+      }
+      g->device_bytes += (int64_t)g->n * 8;
+    }
+    rc = launch_run(g, source, g->out_scratch, g->out_scratch + g->n, s);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(depth, g->out_scratch, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(parent, g->out_scratch + g->n, (size_t)g->n * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy results");
+  }
+  if (!dd || stats) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs_run");
+    RunHeader h;
+    rc = run_status(g, &h);
+    if (rc) return rc;
+    if (stats) return fill_stats(g, stats, h);
+  }
+  return BFS_OK;
+}
+
+extern "C" int bfs_wait(bfs_graph* g, struct CUstream_st* stream) {
+  if (!g) return fail(BFS_ERR_INVALID, "graph is NULL");
+  DeviceGuard dg(g->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs_wait");
+  RunHeader h;
+  return run_status(g, &h);
+}
+
+extern "C" void bfs_free(bfs_graph* g) {
+  if (!g) return;
+  DeviceGuard dg(g->device);
+  cudaDeviceSynchronize();
+  free_all(g);
+  delete g;
+}
+
+extern "C" const char* bfs_last_error(void) { return t_error.c_str(); }
+
+extern "C" void bfs_abi_sizes(int64_t sizes[4]) {
+  sizes[0] = (int64_t)sizeof(bfs_options);
+  sizes[1] = (int64_t)sizeof(bfs_graph_info);
+  sizes[2] = (int64_t)sizeof(bfs_level_log);
+  sizes[3] = (int64_t)sizeof(bfs_stats);
+}

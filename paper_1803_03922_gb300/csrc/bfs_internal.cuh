@@ -1,0 +1,128 @@
+// Internal layout shared by the builder, the level-loop kernel and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bfs_gb300.h"
+
+namespace bfsgb {
+
+constexpr int kThreads = 512;         // level-loop CTA size (16 warps)
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
+constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Per-level counters; a ring of kSlots indexed by level.
+struct __align__(64) LevelSlot {
+  unsigned long long qn;        // normal-queue entries holding this level's frontier
+  unsigned long long nch;       // delegate chunk entries holding this level's frontier
+  unsigned long long n_f;       // frontier vertices
+  unsigned long long m_f;       // frontier degree sum
+  unsigned long long work;      // dynamic work counter of this level's expansion
+  unsigned long long edges;     // backward: sum of k_v
+  unsigned long long scanned;   // backward: unvisited vertices scanned
+  unsigned long long fix_edges; // forward: row entries read to pick parents
+};
+constexpr int kSlots = 4;
+
+struct LevelLogDev {
+  int32_t dir, converted;
+  unsigned long long n_f, m_f, scanned, edges, fix_edges, found, qn;
+  unsigned long long t_begin, t_expand, t_end;
+};
+
+struct RunHeader {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int err;    // (epoch << 4) | -BFS_ERR_*, written by the device on failure
+  unsigned int exited; // CTAs that left the kernel (the last one resets the barrier)
+  int levels;          // levels run
+  int pad;
+  unsigned long long t0, t1;
+  unsigned long long reached_edges;  // sum of m_f over all levels (= 2 x component edges)
+  unsigned long long reached;        // sum of n_f over all levels
+};
+
+// Everything the level-loop kernel reads, by value.
+struct BfsParams {
+  const int64_t* off;        // [n_ni+1]
+  const int32_t* col;        // [nnz + kColPad]
+  const int32_t* caller_of;  // [n]
+  const int32_t* internal_of;// [n]
+  uint32_t* V;               // visited bitmap, [words]
+  uint32_t* N0;              // discovered-this-level bitmaps, [words] each
+  uint32_t* N1;
+  int32_t* depth_i;          // [n_ni]
+  int32_t* parent_i;         // [n_ni], caller ids
+  int32_t* Q0;               // normal-vertex frontier queues, [n_ni] each
+  int32_t* Q1;
+  int2* CL0;                 // delegate chunk lists (vertex, chunk), [cl_cap] each
+  int2* CL1;
+  LevelSlot* slot;           // [kSlots]
+  LevelLogDev* log;          // [BFS_LOG_LEVELS]
+  RunHeader* hdr;
+  int32_t* out_depth;        // [n] caller-indexed
+  int32_t* out_parent;       // [n]
+  int64_t nnz;
+  int64_t words;             // ceil(n_ni / 32)
+  int32_t n, n_ni, d;
+  int32_t src_c;             // source, caller id
+  int32_t schedule;
+  int32_t alpha, beta;
+  int32_t td_parent;
+  uint64_t schedule_mask;
+  double factor0, factor1;
+  unsigned long long timeout_ns;
+  unsigned int epoch;        // run number; tags the status word
+  int32_t test_skip_barrier; // testing only: CTA 0 skips the first barrier
+  unsigned long long run_timeout_ns;
+};
+
+}  // namespace bfsgb
+
+struct bfs_graph {
+  int device = 0;
+  int32_t n = 0, n_ni = 0, d = 0;
+  int64_t th = 0, nnz = 0, max_deg = 0;
+  int64_t sub[4] = {0, 0, 0, 0};
+  int64_t cl_cap = 0;
+  int64_t words = 0;
+  int64_t device_bytes = 0;
+  bfs_options opt{};
+  // graph
+  int64_t* off = nullptr;
+  int32_t* col = nullptr;
+  int32_t* caller_of = nullptr;
+  int32_t* internal_of = nullptr;
+  // run state
+  uint32_t* V = nullptr;
+  uint32_t* N0 = nullptr;
+  uint32_t* N1 = nullptr;
+  int32_t* depth_i = nullptr;
+  int32_t* parent_i = nullptr;
+  int32_t* Q0 = nullptr;
+  int32_t* Q1 = nullptr;
+  int2* CL0 = nullptr;
+  int2* CL1 = nullptr;
+  bfsgb::LevelSlot* slot = nullptr;
+  bfsgb::LevelLogDev* log = nullptr;
+  bfsgb::RunHeader* hdr = nullptr;
+  int32_t* out_scratch = nullptr;  // [2n], for runs with host output buffers
+  int grid_blocks = 0;
+  unsigned int epoch = 0;          // runs launched
+};
+
+namespace bfsgb {
+// Thread-local error text (bfs_last_error).
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+// Level-loop set-up and launch (bfs_run.cu).
+int configure_run(bfs_graph* g);
+int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s);
+int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st);
+}  // namespace bfsgb

@@ -1,0 +1,803 @@
+// Level loop of direction-optimized BFS over a degree-separated graph: one
+// persistent cooperative kernel per BFS run, so no level ever returns to the host.
+//
+// Per level L (frontier F_L = vertices at depth L):
+//   forward (top-down, push; Sec. IV-A): normal vertices of F_L come from an int32
+//     queue and are expanded a warp-batch at a time (one lane owns a vertex, the
+//     warp gathers the 32 rows' entries together); delegates of F_L come from a
+//     list of 512-entry row chunks, so a very high-degree row is spread over many
+//     warps (merge-style partitioning, Sec. IV-A) and read with 128-bit loads.
+//     Every unvisited target sets its bit in the discovered bitmap N; the lane
+//     whose atomicOr set the bit appends it to the next queue or chunk list.
+//   backward (bottom-up, pull; Sec. II-C, IV-B): every unvisited non-isolated
+//     vertex scans its row, which is sorted by caller id, and stops at the first
+//     neighbour already visited; that neighbour is the canonical parent.
+//   level end (fused): N is merged into the visited bitmap V; after a forward
+//     level the parent of each newly reached vertex is picked by the same
+//     first-hit scan over its sorted row (predicate: visited before this level).
+//   direction (Sec. IV-B): chosen from the frontier counters by every CTA alike.
+// When a backward level is followed by a forward one, the bitmap of the new
+// frontier is converted into the queue and chunk list first.
+//
+// Every grid-barrier wait is bounded by a %globaltimer deadline; on expiry the
+// kernel records BFS_ERR_TIMEOUT and every CTA returns.
+#include <climits>
+
+#include "bfs_internal.cuh"
+
+namespace bfsgb {
+namespace {
+
+__device__ __forceinline__ int lane_id() { return (int)(threadIdx.x & 31u); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += t;
+  }
+  return x;
+}
+
+// Status word: (epoch << 4) | code, code = -BFS_ERR_*.
+__device__ __forceinline__ bool run_failed(const BfsParams& p) {
+  unsigned e = *(volatile unsigned*)&p.hdr->err;
+  return e != 0 && (e >> 4) == (p.epoch & 0x0FFFFFFFu);
+}
+
+__device__ __forceinline__ void set_failed(const BfsParams& p, int code) {
+  atomicExch((unsigned*)&p.hdr->err, ((p.epoch & 0x0FFFFFFFu) << 4) | (unsigned)(-code));
+}
+
+// Grid-wide barrier over co-resident CTAs (cooperative launch).  Returns false
+// (uniformly per CTA) if the run failed or the wait passed its deadline.
+__device__ bool grid_sync(const BfsParams& p) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned* cnt = &p.hdr->bar_count;
+    unsigned* gen = &p.hdr->bar_gen;
+    unsigned g0 = ld_acquire(gen);
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = gtimer();
+      while (ld_acquire(gen) == g0) {
+        if (run_failed(p)) {
+          ok = 0;
+          break;
+        }
+        if (gtimer() - t0 > p.timeout_ns) {
+          set_failed(p, BFS_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ok && run_failed(p)) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct Acc {
+  unsigned long long nf = 0, mf = 0, edges = 0, scanned = 0, fix = 0;
+};
+
+// Visited-state probe for the pull scans.  Backward: visited before this level
+// (V is read-only during the expansion).  Parent pick after a forward level:
+// visited and not discovered in this level (V is being merged concurrently; the
+// second test makes the answer the same either way).
+template <bool kFix>
+__device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t* __restrict__ Ncur) {
+  bool s = (p.V[c >> 5] >> (c & 31)) & 1u;
+  if (kFix && s) s = !((__ldcg(Ncur + (c >> 5)) >> (c & 31)) & 1u);
+  return s;
+}
+
+// Pull scan for one vertex per lane: lanes with `act` scan [beg,end) in order and
+// stop at the first neighbour passing the probe.  The first kWin entries are read
+// by the owning lane; rows not settled by then are finished by 8-lane groups,
+// four rows at a time, one 32-byte sector per group and step.
+// Returns the neighbour's internal id or -1; kv = entries examined (first-hit
+// position + 1, or the degree).
+template <bool kFix>
+__device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end,
+                          const uint32_t* __restrict__ Ncur, int64_t& kv) {
+  constexpr int kWin = 4;
+  const int lane = lane_id();
+  int hit = -1;
+  int64_t k = 0;
+  if (act) {
+    const int64_t lim = min(end, beg + kWin);
+    int c[kWin];
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) c[t] = (beg + t < lim) ? p.col[beg + t] : -1;
+#pragma unroll
+    for (int t = 0; t < kWin; ++t)
+      if (hit < 0 && c[t] >= 0 && probe<kFix>(p, c[t], Ncur)) {
+        hit = c[t];
+        k = t + 1;
+      }
+    if (hit < 0) k = lim - beg;
+  }
+  unsigned rem = __ballot_sync(kFull, act && hit < 0 && beg + kWin < end);
+  const int g = lane >> 3, sub = lane & 7;
+  while (rem) {
+    const int take = min(__popc(rem), 4);
+    unsigned r = rem;
+    for (int q = 0; q < g && q < 3; ++q) r &= r - 1;
+    const int srcl = (g < take) ? (__ffs(r) - 1) : 0;
+    const int64_t rbeg = __shfl_sync(kFull, beg, srcl);
+    const int64_t rend = __shfl_sync(kFull, end, srcl);
+    bool gdone = g >= take;
+    int ghit = -1;
+    int64_t gk = 0;
+    int64_t pos = rbeg + kWin;
+    while (__any_sync(kFull, !gdone)) {
+      const int64_t j = pos + sub;
+      const int c = (!gdone && j < rend) ? p.col[j] : -1;
+      const bool h = c >= 0 && probe<kFix>(p, c, Ncur);
+      const unsigned gb = (__ballot_sync(kFull, h) >> (g * 8)) & 0xFFu;
+      const int first = gb ? __ffs(gb) - 1 : 0;
+      const int hc = __shfl_sync(kFull, c, g * 8 + first);
+      if (!gdone) {
+        if (gb) {
+          ghit = hc;
+          gk = pos + first - rbeg + 1;
+          gdone = true;
+        } else {
+          pos += 8;
+          if (pos >= rend) {
+            gdone = true;
+            gk = rend - rbeg;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int h2 = __shfl_sync(kFull, ghit, q * 8);
+      const int64_t k2 = __shfl_sync(kFull, gk, q * 8);
+      const int owner = __shfl_sync(kFull, srcl, q * 8);
+      if (q < take && lane == owner) {
+        hit = h2;
+        k = k2;
+      }
+    }
+    for (int q = 0; q < take; ++q) rem &= rem - 1;
+  }
+  kv = k;
+  return hit;
+}
+
+// Pull scan of one high-degree vertex by the whole warp with 128-bit loads
+// (128 row entries per step).  Same result and kv as pull_lanes.
+template <bool kFix>
+__device__ int warp_pull(const BfsParams& p, int v, const uint32_t* __restrict__ Ncur, int64_t& kv,
+                         int64_t& deg) {
+  const int lane = lane_id();
+  const int64_t beg = p.off[v], end = p.off[v + 1];
+  deg = end - beg;
+  for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 128) {
+    const int64_t j = j0 + lane * 4;
+    unsigned best = 0xFFFFFFFFu;
+    int bc = -1;
+    if (j < end) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
+      const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+      for (int t = 3; t >= 0; --t) {
+        const int64_t idx = j + t;
+        if (idx >= beg && idx < end && probe<kFix>(p, cs[t], Ncur)) {
+          best = (unsigned)(idx - beg);
+          bc = cs[t];
+        }
+      }
+    }
+    const unsigned wbest = __reduce_min_sync(kFull, best);
+    if (wbest != 0xFFFFFFFFu) {
+      const unsigned who = __ballot_sync(kFull, best == wbest);
+      kv = (int64_t)wbest + 1;
+      return __shfl_sync(kFull, bc, __ffs(who) - 1);
+    }
+  }
+  kv = deg;
+  return -1;
+}
+
+// ---- forward level ------------------------------------------------------------------------
+
+struct TdOut {
+  uint32_t* N;   // discovered bitmap of this level
+  int32_t* Qn;   // next normal queue
+  int2* CLn;     // next delegate chunk list
+  LevelSlot* sn; // counters of the next frontier
+  int depth;     // depth of newly reached vertices
+};
+
+// One row entry u->v of a forward visit, called by all 32 lanes together
+// (v < 0: lane idle).  The lane whose atomicOr set v's bit owns v: it writes the
+// depth, adds v's degree to m_f and appends v to the next queue or chunk list.
+__device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, const TdOut& o, Acc& acc) {
+  bool win = false;
+  if (v >= 0) {
+    const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
+    if (!(p.V[w] & bit)) {
+      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
+      if (!(__ldcg(o.N + w) & bit)) win = !(atomicOr(o.N + w, bit) & bit);
+    }
+  }
+  const unsigned wb = __ballot_sync(kFull, win);
+  if (!wb) return;
+  const int lane = lane_id();
+  int64_t deg = 0;
+  if (win) {
+    deg = p.off[v + 1] - p.off[v];
+    p.depth_i[v] = o.depth;
+    acc.nf += 1;
+    acc.mf += (unsigned long long)deg;
+  }
+  const bool isn = win && v >= p.d;
+  const unsigned nb = __ballot_sync(kFull, isn);
+  if (nb) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&o.sn->qn, (unsigned long long)__popc(nb));
+    base = __shfl_sync(kFull, base, 0);
+    if (isn) o.Qn[base + __popc(nb & ((1u << lane) - 1u))] = v;
+  }
+  const bool isd = win && v < p.d;
+  if (__ballot_sync(kFull, isd)) {
+    const int64_t nch = isd ? (deg + kChunk - 1) / kChunk : 0;
+    const int64_t incl = warp_incl_scan(nch);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&o.sn->nch, (unsigned long long)incl);
+    base = __shfl_sync(kFull, base, 31);
+    if (isd)
+      for (int64_t k = 0; k < nch; ++k) o.CLn[base + (incl - nch) + k] = make_int2(v, (int)k);
+  }
+}
+
+// 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
+// concatenation of the 32 rows 32 entries at a time.
+__device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int64_t qn, int64_t b,
+                         const TdOut& o, Acc& acc) {
+  const int lane = lane_id();
+  const int64_t i = b * 32 + lane;
+  const int u = i < qn ? Qc[i] : -1;
+  int64_t beg = 0, deg = 0;
+  int pc = 0;
+  if (u >= 0) {
+    beg = p.off[u];
+    deg = p.off[u + 1] - beg;
+    if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) pc = p.caller_of[u];
+  }
+  const int64_t incl = warp_incl_scan(deg);
+  const int64_t total = __shfl_sync(kFull, incl, 31);
+  const int64_t excl = incl - deg;
+  for (int64_t base = 0; base < total; base += 32) {
+    const int64_t e = base + lane;
+    int pos = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const int64_t t = __shfl_sync(kFull, incl, pos + s - 1);
+      if (t <= e) pos += s;
+    }
+    const int64_t ob = __shfl_sync(kFull, beg, pos);
+    const int64_t ox = __shfl_sync(kFull, excl, pos);
+    const int opc = __shfl_sync(kFull, pc, pos);
+    const int v = e < total ? p.col[ob + (e - ox)] : -1;
+    td_edge(p, v, opc, o, acc);
+  }
+}
+
+// One 512-entry chunk of a delegate's row, 128-bit loads.
+__device__ void td_chunk(const BfsParams& p, int2 ck, const TdOut& o, Acc& acc) {
+  const int lane = lane_id();
+  const int u = ck.x;
+  const int64_t rb = p.off[u], re = p.off[u + 1];
+  const int64_t beg = rb + (int64_t)ck.y * kChunk;
+  const int64_t end = min(beg + kChunk, re);
+  const int pc = (p.td_parent == BFS_TD_PARENT_ATOMICMIN) ? p.caller_of[u] : 0;
+  for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 128) {
+    const int64_t j = j0 + lane * 4;
+    int4 c4 = make_int4(-1, -1, -1, -1);
+    if (j < end) c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
+    const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int64_t idx = j + t;
+      td_edge(p, (idx >= beg && idx < end) ? cs[t] : -1, pc, o, acc);
+    }
+  }
+}
+
+__device__ __forceinline__ long long grab(unsigned long long* ctr) {
+  unsigned long long x = 0;
+  if (lane_id() == 0) x = atomicAdd(ctr, 1ull);
+  return (long long)__shfl_sync(kFull, x, 0);
+}
+
+__device__ void expand_td(const BfsParams& p, int L, Acc& acc) {
+  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  const int64_t qn = (int64_t)__ldcg(&sc->qn);
+  const int64_t nch = (int64_t)__ldcg(&sc->nch);
+  const int64_t nb = (qn + 31) / 32;
+  const int32_t* Qc = (L & 1) ? p.Q1 : p.Q0;
+  const int2* CLc = (L & 1) ? p.CL1 : p.CL0;
+  TdOut o;
+  o.N = (L & 1) ? p.N1 : p.N0;
+  o.Qn = (L & 1) ? p.Q0 : p.Q1;
+  o.CLn = (L & 1) ? p.CL0 : p.CL1;
+  o.sn = p.slot + ((L + 1) & (kSlots - 1));
+  o.depth = L + 1;
+  const int64_t total = nch + nb;
+  for (long long it = grab(&sc->work); it < total; it = grab(&sc->work)) {
+    if (it < nch)
+      td_chunk(p, CLc[it], o, acc);
+    else
+      td_batch(p, Qc, qn, it - nch, o, acc);
+  }
+}
+
+// ---- backward level -----------------------------------------------------------------------
+
+// Unvisited vertices of one 32-vertex word; returns the mask of those that found
+// a parent.  Delegates (high degree) are scanned by the whole warp, normal
+// vertices by pull_lanes.
+__device__ unsigned bu_word(const BfsParams& p, int64_t word, unsigned m, int L, Acc& acc) {
+  const int lane = lane_id();
+  const int64_t v0 = word * 32;
+  unsigned dmask = 0;
+  if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
+  unsigned found = 0;
+  unsigned md = m & dmask;
+  while (md) {
+    const int i = __ffs(md) - 1;
+    md &= md - 1;
+    const int v = (int)(v0 + i);
+    int64_t kv, deg;
+    const int hit = warp_pull<false>(p, v, nullptr, kv, deg);
+    if (lane == 0) {
+      acc.scanned += 1;
+      acc.edges += (unsigned long long)kv;
+      if (hit >= 0) {
+        p.parent_i[v] = p.caller_of[hit];
+        p.depth_i[v] = L + 1;
+        acc.nf += 1;
+        acc.mf += (unsigned long long)deg;
+      }
+    }
+    if (hit >= 0) found |= 1u << i;
+  }
+  const unsigned mn = m & ~dmask;
+  const bool act = (mn >> lane) & 1u;
+  const int v = (int)(v0 + lane);
+  int64_t beg = 0, end = 0;
+  if (act) {
+    beg = p.off[v];
+    end = p.off[v + 1];
+  }
+  int64_t kv = 0;
+  const int hit = pull_lanes<false>(p, act, beg, end, nullptr, kv);
+  if (act) {
+    acc.scanned += 1;
+    acc.edges += (unsigned long long)kv;
+    if (hit >= 0) {
+      p.parent_i[v] = p.caller_of[hit];
+      p.depth_i[v] = L + 1;
+      acc.nf += 1;
+      acc.mf += (unsigned long long)(end - beg);
+    }
+  }
+  found |= __ballot_sync(kFull, act && hit >= 0);
+  return found;
+}
+
+__device__ void expand_bu(const BfsParams& p, int L, Acc& acc) {
+  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  uint32_t* N = (L & 1) ? p.N1 : p.N0;
+  const int lane = lane_id();
+  const int64_t W = p.words;
+  const int64_t groups = (W + 31) / 32;
+  const int tail = p.n_ni & 31;
+  for (long long gi = grab(&sc->work); gi < groups; gi = grab(&sc->work)) {
+    const int64_t w = gi * 32 + lane;
+    unsigned vis = kFull;
+    if (w < W) {
+      vis = p.V[w];
+      if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
+    }
+    const unsigned unv = ~vis;
+    unsigned pend = __ballot_sync(kFull, unv != 0);
+    while (pend) {
+      const int j = __ffs(pend) - 1;
+      pend &= pend - 1;
+      const unsigned m = __shfl_sync(kFull, unv, j);
+      const unsigned f = bu_word(p, gi * 32 + j, m, L, acc);
+      if (lane == 0 && f) N[gi * 32 + j] = f;
+    }
+  }
+}
+
+// ---- level end and conversions -------------------------------------------------------------
+
+// Merge N into V and clear the other N buffer; after a forward level with PULL
+// parents, pick each new vertex's parent by a first-hit scan of its sorted row.
+__device__ void level_end(const BfsParams& p, int L, bool td, Acc& acc) {
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+  uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
+  for (int64_t w = gtid; w < p.words; w += gthreads) {
+    const unsigned nb = __ldcg(Ncur + w);
+    if (nb) p.V[w] |= nb;
+    Noth[w] = 0;
+  }
+  if (td && p.td_parent == BFS_TD_PARENT_PULL) {
+    const LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
+    const int64_t qn = (int64_t)__ldcg(&sn->qn);
+    const int64_t nch = (int64_t)__ldcg(&sn->nch);
+    const int32_t* Qn = (L & 1) ? p.Q0 : p.Q1;
+    const int2* CLn = (L & 1) ? p.CL0 : p.CL1;
+    const int lane = lane_id();
+    const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
+    for (int64_t b = gwarp; b * 32 < qn; b += nwarps) {
+      const int64_t i = b * 32 + lane;
+      const bool act = i < qn;
+      const int v = act ? Qn[i] : 0;
+      int64_t beg = 0, end = 0;
+      if (act) {
+        beg = p.off[v];
+        end = p.off[v + 1];
+      }
+      int64_t kv = 0;
+      const int hit = pull_lanes<true>(p, act, beg, end, Ncur, kv);
+      if (act) {
+        acc.fix += (unsigned long long)kv;
+        if (hit >= 0) p.parent_i[v] = p.caller_of[hit];
+      }
+    }
+    for (int64_t e = gwarp; e < nch; e += nwarps) {
+      const int2 ck = CLn[e];
+      if (ck.y != 0) continue;
+      int64_t kv, deg;
+      const int hit = warp_pull<true>(p, ck.x, Ncur, kv, deg);
+      if (lane == 0) {
+        acc.fix += (unsigned long long)kv;
+        if (hit >= 0) p.parent_i[ck.x] = p.caller_of[hit];
+      }
+    }
+  }
+}
+
+// Frontier F_L held as the bitmap of level L-1's discoveries -> queue + chunk list.
+__device__ void convert_to_queues(const BfsParams& p, int L) {
+  const uint32_t* Nf = (L & 1) ? p.N0 : p.N1;  // discoveries of level L-1
+  int32_t* Q = (L & 1) ? p.Q1 : p.Q0;
+  int2* CL = (L & 1) ? p.CL1 : p.CL0;
+  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  const int lane = lane_id();
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t Wr = (p.words + 31) & ~(int64_t)31;  // warp-uniform trip count
+  for (int64_t w = gtid; w < Wr; w += gthreads) {
+    const unsigned nb = w < p.words ? __ldcg(Nf + w) : 0u;
+    const int64_t v0 = w * 32;
+    unsigned dmask = 0;
+    if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
+    const unsigned nn = nb & ~dmask;
+    const int64_t cnt = __popc(nn);
+    const int64_t incl = warp_incl_scan(cnt);
+    unsigned long long base = 0;
+    if (lane == 31 && incl) base = atomicAdd(&sc->qn, (unsigned long long)incl);
+    base = __shfl_sync(kFull, base, 31) + (incl - cnt);
+    unsigned x = nn;
+    while (x) {
+      const int i = __ffs(x) - 1;
+      x &= x - 1;
+      Q[base++] = (int)(v0 + i);
+    }
+    unsigned dd = nb & dmask;
+    while (dd) {
+      const int i = __ffs(dd) - 1;
+      dd &= dd - 1;
+      const int v = (int)(v0 + i);
+      const int64_t deg = p.off[v + 1] - p.off[v];
+      const int64_t nch = (deg + kChunk - 1) / kChunk;
+      const unsigned long long b = atomicAdd(&sc->nch, (unsigned long long)nch);
+      for (int64_t k = 0; k < nch; ++k) CL[b + k] = make_int2(v, (int)k);
+    }
+  }
+}
+
+__device__ void flush_acc(Acc& a, unsigned long long* nf, unsigned long long* mf, unsigned long long* edges,
+                          unsigned long long* scanned, unsigned long long* fix) {
+  const unsigned long long x0 = warp_sum(a.nf), x1 = warp_sum(a.mf), x2 = warp_sum(a.edges),
+                           x3 = warp_sum(a.scanned), x4 = warp_sum(a.fix);
+  if (lane_id() == 0) {
+    if (x0 && nf) atomicAdd(nf, x0);
+    if (x1 && mf) atomicAdd(mf, x1);
+    if (x2 && edges) atomicAdd(edges, x2);
+    if (x3 && scanned) atomicAdd(scanned, x3);
+    if (x4 && fix) atomicAdd(fix, x4);
+  }
+  a = Acc();
+}
+
+// Direction of level L+1 from its frontier (Sec. IV-B), computed alike by every CTA.
+__device__ int decide(const BfsParams& p, int L1, int cur, unsigned long long nf, unsigned long long mf,
+                      unsigned long long prev_nf, long long m_u, long long unvisited) {
+  switch (p.schedule) {
+    case BFS_SCHED_TOPDOWN:
+      return 0;
+    case BFS_SCHED_BOTTOMUP:
+      return L1 >= 1 ? 1 : 0;
+    case BFS_SCHED_ALTERNATE:
+      return L1 & 1;
+    case BFS_SCHED_MASK:
+      return (int)((p.schedule_mask >> (L1 < 63 ? L1 : 63)) & 1ull);
+    case BFS_SCHED_PAPER: {
+      // FV = frontier degree sum; BV = |U| (q + s) / q with q = |frontier| and
+      // U = s = unvisited vertices (one symmetric graph on one GPU).
+      const double q = (double)nf, s = (double)(unvisited > 0 ? unvisited : 0);
+      const double fv = (double)mf, bv = s * (q + s) / q;
+      if (cur == 0) return fv > p.factor0 * bv ? 1 : 0;
+      return fv < p.factor1 * bv ? 0 : 1;
+    }
+    default: {  // Beamer alpha/beta
+      if (cur == 0) return (long long)(mf * (unsigned long long)p.alpha) > m_u ? 1 : 0;
+      const bool small = nf * (unsigned long long)p.beta < (unsigned long long)p.n;
+      return (small && nf < prev_nf) ? 0 : 1;
+    }
+  }
+}
+
+__device__ void run_body(const BfsParams& p);
+
+// Every CTA passes here on exit, normal or not; the last one leaves the barrier
+// counter at zero for the next run.
+__device__ void block_exit(const BfsParams& p) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&p.hdr->exited, 1u) == gridDim.x - 1) {
+      atomicExch(&p.hdr->bar_count, 0u);
+      atomicExch(&p.hdr->exited, 0u);
+      __threadfence();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) bfs_level_loop(BfsParams p) {
+  run_body(p);
+  block_exit(p);
+}
+
+__device__ void run_body(const BfsParams& p) {
+  __shared__ int s_dir, s_done, s_conv;
+  __shared__ long long s_mu, s_unv;
+  __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  Acc acc;
+
+  // ---- init: clear bitmaps, seed the source ----
+  const int src_i = p.internal_of[p.src_c];
+  const bool src_in = src_i < p.n_ni;
+  const int64_t sw = src_in ? (src_i >> 5) : -1;
+  const unsigned sbit = 1u << (src_i & 31);
+  for (int64_t w = gtid; w < p.words; w += gthreads) {
+    p.V[w] = (w == sw) ? sbit : 0u;
+    p.N0[w] = 0u;
+    p.N1[w] = 0u;
+  }
+  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN)
+    for (int64_t v = gtid; v < p.n_ni; v += gthreads) p.parent_i[v] = (v == src_i) ? p.src_c : INT_MAX;
+  unsigned long long src_deg = 0;
+  if (src_in) src_deg = (unsigned long long)(p.off[src_i + 1] - p.off[src_i]);
+  if (leader) {
+    for (int k = 0; k < kSlots; ++k) p.slot[k] = LevelSlot();
+    p.hdr->t0 = gtimer();
+    if (src_in) {
+      p.depth_i[src_i] = 0;
+      p.parent_i[src_i] = p.src_c;
+      p.slot[0].n_f = 1;
+      p.slot[0].m_f = src_deg;
+      if (src_i >= p.d) {
+        p.Q0[0] = src_i;
+        p.slot[0].qn = 1;
+      } else {
+        const int64_t nch = ((int64_t)src_deg + kChunk - 1) / kChunk;
+        for (int64_t k = 0; k < nch; ++k) p.CL0[k] = make_int2(src_i, (int)k);
+        p.slot[0].nch = (unsigned long long)nch;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    s_done = src_in ? 0 : 1;
+    s_mu = (long long)p.nnz - (long long)src_deg;
+    s_unv = (long long)p.n_ni - (src_in ? 1 : 0);
+    s_prev_nf = 1;
+    s_reach_e = src_deg;
+    s_reach_v = 1;
+    s_dir = decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv);
+    s_conv = 0;
+  }
+  if (p.test_skip_barrier && blockIdx.x == 0) return;  // the others' bounded wait must expire
+  if (!grid_sync(p)) return;
+
+  const unsigned long long t_start = gtimer();
+  int L = 0;
+  while (!s_done) {
+    // Bounds against a run that does not end: at most n_ni+1 levels, and the
+    // run's deadline.  A failure set here ends every CTA at its next barrier.
+    if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
+      set_failed(p, BFS_ERR_TIMEOUT);
+    const int dir = s_dir;
+    if (s_conv) {
+      convert_to_queues(p, L);
+      if (!grid_sync(p)) return;
+    }
+    if (leader) s_tb = gtimer();
+    LevelSlot* sc = p.slot + (L & (kSlots - 1));
+    LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
+    if (dir == 0) {
+      expand_td(p, L, acc);
+      flush_acc(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+    } else {
+      expand_bu(p, L, acc);
+      flush_acc(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
+    }
+    if (!grid_sync(p)) return;
+    if (leader) s_te = gtimer();
+    level_end(p, L, dir == 0, acc);
+    flush_acc(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+    if (leader) p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+    if (!grid_sync(p)) return;
+    if (threadIdx.x == 0) {
+      const unsigned long long nf = __ldcg(&sn->n_f), mf = __ldcg(&sn->m_f);
+      if (leader && L < BFS_LOG_LEVELS) {
+        LevelLogDev& lg = p.log[L];
+        lg.dir = dir;
+        lg.converted = s_conv;
+        lg.n_f = __ldcg(&sc->n_f);
+        lg.m_f = __ldcg(&sc->m_f);
+        lg.scanned = __ldcg(&sc->scanned);
+        lg.edges = dir == 0 ? __ldcg(&sc->m_f) : __ldcg(&sc->edges);
+        lg.fix_edges = __ldcg(&sc->fix_edges);
+        lg.found = nf;
+        lg.qn = __ldcg(&sc->qn);
+        lg.t_begin = s_tb;
+        lg.t_expand = s_te;
+        lg.t_end = gtimer();
+      }
+      s_mu -= (long long)mf;
+      s_unv -= (long long)nf;
+      s_reach_e += mf;
+      s_reach_v += nf;
+      if (nf == 0) {
+        s_done = 1;
+      } else {
+        const int nd = decide(p, L + 1, dir, nf, mf, s_prev_nf, s_mu, s_unv);
+        s_conv = (nd == 0 && dir == 1) ? 1 : 0;
+        s_dir = nd;
+        s_prev_nf = nf;
+      }
+    }
+    __syncthreads();
+    ++L;
+  }
+
+  // ---- results in caller ids ----
+  for (int64_t c = gtid; c < p.n; c += gthreads) {
+    const int v = p.internal_of[c];
+    const bool r = v < p.n_ni && ((p.V[v >> 5] >> (v & 31)) & 1u);
+    int dv = r ? p.depth_i[v] : -1;
+    int pv = r ? p.parent_i[v] : -1;
+    if (c == p.src_c) {
+      dv = 0;
+      pv = p.src_c;
+    }
+    p.out_depth[c] = dv;
+    p.out_parent[c] = pv;
+  }
+  if (leader) {
+    p.hdr->levels = src_in ? L : 1;
+    p.hdr->t1 = gtimer();
+    p.hdr->reached_edges = src_in ? s_reach_e : 0;
+    p.hdr->reached = src_in ? s_reach_v : 1;
+  }
+}
+
+}  // namespace
+
+int configure_run(bfs_graph* g) {
+  int sms = 0, per_sm = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+  if (!coop) return fail(BFS_ERR_CUDA, "device does not support cooperative launch");
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop, kThreads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (per_sm < 1) return fail(BFS_ERR_CUDA, "level-loop kernel does not fit on an SM");
+  int want = g->opt.blocks_per_sm > 0 ? g->opt.blocks_per_sm : per_sm;
+  if (want > per_sm) want = per_sm;
+  g->grid_blocks = sms * want;
+  return BFS_OK;
+}
+
+int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s) {
+  BfsParams p;
+  p.off = g->off;
+  p.col = g->col;
+  p.caller_of = g->caller_of;
+  p.internal_of = g->internal_of;
+  p.V = g->V;
+  p.N0 = g->N0;
+  p.N1 = g->N1;
+  p.depth_i = g->depth_i;
+  p.parent_i = g->parent_i;
+  p.Q0 = g->Q0;
+  p.Q1 = g->Q1;
+  p.CL0 = g->CL0;
+  p.CL1 = g->CL1;
+  p.slot = g->slot;
+  p.log = g->log;
+  p.hdr = g->hdr;
+  p.out_depth = out_depth;
+  p.out_parent = out_parent;
+  p.nnz = g->nnz;
+  p.words = g->words;
+  p.n = g->n;
+  p.n_ni = g->n_ni;
+  p.d = g->d;
+  p.src_c = source;
+  p.schedule = g->opt.schedule;
+  p.alpha = g->opt.alpha;
+  p.beta = g->opt.beta;
+  p.td_parent = g->opt.td_parent;
+  p.schedule_mask = g->opt.schedule_mask;
+  p.factor0 = g->opt.factor0;
+  p.factor1 = g->opt.factor1;
+  p.timeout_ns = (unsigned long long)g->opt.barrier_timeout_ms * 1000000ull;
+  p.test_skip_barrier = g->opt.test_skip_barrier;
+  p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
+  p.epoch = ++g->epoch & 0x0FFFFFFFu;
+  if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
+  void* args[] = {&p};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)bfs_level_loop, dim3(g->grid_blocks), dim3(kThreads),
+                                              args, 0, s);
+  if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
+  return BFS_OK;
+}
+
+}  // namespace bfsgb

@@ -376,12 +376,39 @@ def pin_batch_u8(lib):
     return int(D.max()) == 150
 
 
+def pin_level_counters_closed_forms(lib):
+    """Path 0-1-...-(n-1) from vertex 0, every level backward: at level L the
+    unvisited vertices are L+1..n-1; L+1 finds L at its first entry, every later
+    vertex reads its whole row (degree 2, the last one degree 1)."""
+    n = 12
+    g = _g(n, [(i, i + 1) for i in range(n - 1)], lib)
+    d, _ = g.bfs(0)
+    levels = n
+    dirs = np.ones(levels, dtype=np.int32)
+    c = g.level_counters(0, d, 64, dirs)
+    for L in range(levels):
+        unv = list(range(L + 1, n))
+        want_edges = sum(1 if v == L + 1 else (1 if v == n - 1 else 2) for v in unv)
+        want = [1, 1 if L in (0, n - 1) else 2, 1 if L + 1 < n else 0, len(unv), want_edges, 0, 0]
+        if list(c[L]) != want:
+            return False
+    # star from the centre, forward: level 0 frontier {c} (a normal vertex only if
+    # its degree <= th), all leaves found, each leaf's only neighbour is c
+    m = 9
+    g = _g(m, [(0, v) for v in range(1, m)], lib)
+    d, _ = g.bfs(0)
+    c = g.level_counters(0, d, 4, np.array([0, 0], np.int32))
+    ok = list(c[0]) == [1, m - 1, m - 1, 0, 0, m - 1, 0] and list(c[1]) == [m - 1, m - 1, 0, 0, 0, 0, m - 1]
+    c2 = g.level_counters(0, d, 100, np.array([0, 1], np.int32))
+    return ok and c2[0][6] == 1 and list(c2[1][3:5]) == [0, 0]
+
+
 PINS = [
     pin_path_end, pin_path_middle, pin_star, pin_grid, pin_binary_tree, pin_complete,
     pin_even_cycle, pin_components_and_isolated, pin_dedup_selfloops, pin_exhaustive_5,
     pin_random_small_floyd, pin_scipy_depth_components, pin_invariants_python,
     pin_validator_detects, pin_component_edges, pin_builder_sets, pin_separation,
-    pin_subgraph_counts, pin_batch_u8,
+    pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms,
 ]
 
 

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every symbol its header declares
+(no GPU; no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            for m in re.finditer(r"^\s*(?:int|void|const char\*)\s+(bfs_\w+)\s*\(", txt, flags=re.M):
+                names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1803_03922_gb300 as bfs
+
+    lib = ctypes.CDLL(bfs.library_path())
+    names = _declared()
+    assert {"bfs_build_graph", "bfs_run", "bfs_free", "bfs_last_error"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_binding():
+    import paper_1803_03922_gb300 as bfs
+
+    bfs._load()  # raises on any size mismatch
+
+
+def test_options_default_and_errors_without_gpu():
+    import paper_1803_03922_gb300 as bfs
+
+    o = bfs.bfs_options_default()
+    assert (o.th, o.alpha, o.beta, o.schedule, o.td_parent) == (64, 15, 18, 0, 0)
+    assert o.barrier_timeout_ms == 2000
+    h = ctypes.c_void_p()
+    lib = bfs._load()
+    # argument checks happen before any device call
+    assert lib.bfs_build_graph(None, None, 0, 0, None, ctypes.byref(h), None) == bfs.BFS_ERR_INVALID
+    assert "num_vertices" in bfs.bfs_last_error()
+    assert lib.bfs_run(None, 0, None, None, None, None) == bfs.BFS_ERR_INVALID
+    lib.bfs_free(None)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1803_03922_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "oracle.h" not in txt and "liboracle" not in txt, f
