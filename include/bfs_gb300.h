@@ -136,7 +136,7 @@ typedef struct bfs_level_log {
 
 typedef struct bfs_stats {
   int32_t levels;          /* levels run (= max depth + 1) */
-  int32_t logged_levels;   /* min(levels, BFS_LOG_LEVELS) */
+  int32_t logged_levels;   /* min(levels executed, BFS_LOG_LEVELS); 0 for an isolated source */
   int64_t reached;         /* vertices with depth >= 0 */
   int64_t component_edges; /* unique undirected edges in the traversed component (GTEPS numerator) */
   int64_t edges_examined;  /* sum over levels */

@@ -222,6 +222,7 @@ class Graph:
         opt.th = th
         for k, v in options.items():
             setattr(opt, k, v)
+        self.options = dict(options)
         self._h = bfs_build_graph(src, dst, num_vertices, opt, stream)
         self.info = bfs_graph_get_info(self._h)
         self.n = self.info.n
@@ -235,6 +236,7 @@ class Graph:
         for k, v in options.items():
             setattr(opt, k, v)
         bfs_set_options(self._h, opt)
+        self.options = dict(options)
 
     def export(self):
         return bfs_graph_export(self._h)

@@ -247,7 +247,7 @@ extern "C" int bfs_graph_export(const bfs_graph* g, int64_t* row_off, int32_t* c
 static int fill_stats(bfs_graph* g, bfs_stats* st, const RunHeader& h) {
   std::memset(st, 0, sizeof(*st));
   st->levels = h.levels;
-  st->logged_levels = h.levels < BFS_LOG_LEVELS ? h.levels : BFS_LOG_LEVELS;
+  st->logged_levels = h.levels_run < BFS_LOG_LEVELS ? h.levels_run : BFS_LOG_LEVELS;
   st->reached = (int64_t)h.reached;
   st->component_edges = (int64_t)(h.reached_edges / 2);
   st->device_ns = h.t1 - h.t0;

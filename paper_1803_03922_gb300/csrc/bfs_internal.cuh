@@ -40,8 +40,8 @@ struct RunHeader {
   unsigned int bar_gen;
   unsigned int err;    // (epoch << 4) | -BFS_ERR_*, written by the device on failure
   unsigned int exited; // CTAs that left the kernel (the last one resets the barrier)
-  int levels;          // levels run
-  int pad;
+  int levels;          // max depth + 1
+  int levels_run;      // levels executed by the loop (0 for an isolated source)
   unsigned long long t0, t1;
   unsigned long long reached_edges;  // sum of m_f over all levels (= 2 x component edges)
   unsigned long long reached;        // sum of n_f over all levels

@@ -731,6 +731,7 @@ __device__ void run_body(const BfsParams& p) {
   }
   if (leader) {
     p.hdr->levels = src_in ? L : 1;
+    p.hdr->levels_run = L;
     p.hdr->t1 = gtimer();
     p.hdr->reached_edges = src_in ? s_reach_e : 0;
     p.hdr->reached = src_in ? s_reach_v : 1;
