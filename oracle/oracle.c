@@ -17,51 +17,58 @@ struct orc_graph {
   int32_t* col; /* nnz, each row ascending, no duplicates, no self-loops */
 };
 
-static int cmp_i32(const void* a, const void* b) {
-  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
-  return (x > y) - (x < y);
-}
-
 /* Sec. II-B: the graph is symmetric; Sec. VI-A.3: the undirected graph is made
- * by edge doubling.  Self-loops are dropped and duplicate pairs kept once. */
+ * by edge doubling.  Self-loops are dropped and duplicate pairs kept once.
+ * Rows are sorted by a two-pass bucket sort: every directed entry u->v is first
+ * placed in the bucket of its target v, then the buckets are read in ascending v
+ * and each entry appended to row u, so every row receives its targets in
+ * ascending order; equal neighbours are then adjacent and kept once. */
 orc_graph* orc_graph_build(int32_t n, int64_t m, const int32_t* src, const int32_t* dst) {
   if (n <= 0 || m < 0 || (m > 0 && (!src || !dst))) return NULL;
   for (int64_t e = 0; e < m; ++e)
     if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n) return NULL;
 
+  /* step 1: entries per vertex; the graph is symmetric, so a vertex is the
+   * source of as many entries as it is the target of */
   int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
   if (!cnt) return NULL;
-  /* step 1: count both directions of every non-loop edge */
   for (int64_t e = 0; e < m; ++e) {
     int32_t u = src[e], v = dst[e];
     if (u == v) continue;
     cnt[u] += 1;
     cnt[v] += 1;
   }
-  /* step 2: row starts */
   int64_t* start = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
   if (!start) { free(cnt); return NULL; }
   start[0] = 0;
   for (int32_t u = 0; u < n; ++u) start[u + 1] = start[u] + cnt[u];
   int64_t total = start[n];
+  int32_t* bucket = (int32_t*)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
   int32_t* raw = (int32_t*)malloc((size_t)(total > 0 ? total : 1) * sizeof(int32_t));
-  if (!raw) { free(cnt); free(start); return NULL; }
-  /* step 3: place u->v and v->u */
+  if (!bucket || !raw) { free(cnt); free(start); free(bucket); free(raw); return NULL; }
+  /* step 2: bucket of target v holds the sources of the entries u->v */
   for (int32_t u = 0; u < n; ++u) cnt[u] = start[u];
   for (int64_t e = 0; e < m; ++e) {
     int32_t u = src[e], v = dst[e];
     if (u == v) continue;
-    raw[cnt[u]++] = v;
-    raw[cnt[v]++] = u;
+    bucket[cnt[v]++] = u; /* entry u->v */
+    bucket[cnt[u]++] = v; /* entry v->u */
   }
-  /* step 4: sort each row, keep each neighbour once */
+  /* step 3: read targets in ascending order, append each entry to its source row */
+  for (int32_t u = 0; u < n; ++u) cnt[u] = start[u];
+  for (int32_t v = 0; v < n; ++v)
+    for (int64_t i = start[v]; i < start[v + 1]; ++i) {
+      int32_t u = bucket[i];
+      raw[cnt[u]++] = v;
+    }
+  free(bucket);
+  /* step 4: keep each neighbour once (rows are sorted) */
   int64_t* off = (int64_t*)malloc(((size_t)n + 1) * sizeof(int64_t));
   if (!off) { free(cnt); free(start); free(raw); return NULL; }
   int64_t w = 0;
   off[0] = 0;
   for (int32_t u = 0; u < n; ++u) {
     int64_t b = start[u], e = start[u + 1];
-    if (e > b) qsort(raw + b, (size_t)(e - b), sizeof(int32_t), cmp_i32);
     for (int64_t i = b; i < e; ++i) {
       if (i > b && raw[i] == raw[i - 1]) continue;
       raw[w++] = raw[i];

@@ -21,9 +21,10 @@ MUTANTS = [
     ("parent_max", "(best == -1 || u < best)", "(best == -1 || u > best)"),
     ("parent_any_level", "if (depth[u] == depth[v] - 1 && (best", "if (depth[u] >= 0 && (best"),
     ("no_dedup", "if (i > b && raw[i] == raw[i - 1]) continue;", ""),
-    ("keep_self_loops", ["    if (u == v) continue;\n    raw[cnt[u]++] = v;", "    if (u == v) continue;\n    cnt[u] += 1;"],
-     ["    raw[cnt[u]++] = v;", "    cnt[u] += 1;"]),
-    ("one_direction", "    raw[cnt[v]++] = u;\n", "    raw[cnt[v]++] = -0 + v;\n"),
+    ("keep_self_loops", ["    if (u == v) continue;\n    bucket[cnt[v]++] = u;", "    if (u == v) continue;\n    cnt[u] += 1;"],
+     ["    bucket[cnt[v]++] = u;", "    cnt[u] += 1;"]),
+    ("one_direction", "    bucket[cnt[u]++] = v; /* entry v->u */", "    bucket[cnt[u]++] = u; /* entry v->u */"),
+    ("rows_unsorted", "  for (int32_t v = 0; v < n; ++v)\n    for (int64_t i = start[v];", "  for (int32_t v = n - 1; v >= 0; --v)\n    for (int64_t i = start[v];"),
     ("depth_plus_two", "depth[v] = depth[u] + 1;", "depth[v] = depth[u] + 2;"),
     ("lifo_queue", "int32_t u = queue[head++];", "int32_t u = queue[--tail];"),
     ("source_parent", "if (v == s) { parent[v] = s; continue; }", "if (v == s) { parent[v] = -1; continue; }"),
