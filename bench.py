@@ -1,0 +1,503 @@
+#!/usr/bin/env python3
+"""Benchmark: single-source direction-optimized BFS over a degree-separated graph
+on one GB300, GTEPS as the harmonic mean over 64 seeded sources.
+
+Workload (default): RMAT scale 22 (4,194,304 vertices, edge factor 16, a,b,c,d =
+.57,.19,.19,.05, ids permuted, self-loops and duplicates removed), degree
+threshold TH = 64, Beamer alpha = 15 / beta = 18, 64 seeded non-isolated sources.
+A step is one BFS from each of the 64 sources.  GTEPS per run = unique undirected
+edges of the traversed component / device time of the run (CUDA events on the
+launching stream); the reported value is their harmonic mean.  The graph build is
+set-up, not timed (Graph500 convention).  The L2 is flushed (256 MiB write)
+before every timed run.
+
+Also reported on the same line: the TH sweep 32/64/128/256 at scale 22, RMAT
+scale 26 and an Erdos-Renyi graph of 2^26 vertices / average degree 32 (device
+numbers), the end-to-end form with host result buffers, the roofline of the
+level-loop kernel against the measured HBM bandwidth, the device clocks during
+the timed region, and the CPU oracle timed on the host as a reference.
+
+`--impl reference` times the CPU oracle alone on the same workload.
+Multi-GPU (torchrun): independent replicas, one graph per GPU, no data exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GTEPS (harmonic mean, 64 sources) at 1 GB300"
+L2_FLUSH_BYTES = 256 << 20
+N_SOURCES = 64
+
+WORKLOADS = {
+    "rmat22": dict(kind="rmat", scale=22, th=64, seed=22, src_seed=2201),
+    "rmat26": dict(kind="rmat", scale=26, th=64, seed=26, src_seed=2601),
+    "er26": dict(kind="er", scale=26, avgdeg=32, th=64, seed=126, src_seed=12601),
+    "rmat16": dict(kind="rmat", scale=16, th=64, seed=16, src_seed=1601),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---- inputs ---------------------------------------------------------------------------------
+
+def make_edges_device(w):
+    import graphgen
+
+    if w["kind"] == "rmat":
+        return graphgen.rmat_device(w["scale"], seed=w["seed"])
+    n = 1 << w["scale"]
+    return graphgen.er_device(n, n * w["avgdeg"] // 2, seed=w["seed"])
+
+
+def make_edges_host(w):
+    import graphgen
+
+    if w["kind"] == "rmat":
+        return graphgen.rmat_host(w["scale"], seed=w["seed"])
+    n = 1 << w["scale"]
+    return graphgen.er_host(n, n * w["avgdeg"] // 2, seed=w["seed"])
+
+
+def sources_for(w, mask, rank=0):
+    import graphgen
+
+    return graphgen.sample_sources(mask, N_SOURCES, seed=w["src_seed"] + 7919 * rank)
+
+
+def hmean(xs):
+    xs = [x for x in xs if x > 0]
+    return len(xs) / sum(1.0 / x for x in xs) if xs else 0.0
+
+
+def gmean(xs):
+    xs = [x for x in xs if x > 0]
+    return math.exp(sum(math.log(x) for x in xs) / len(xs)) if xs else 0.0
+
+
+# ---- clocks during the timed region ---------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_id)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch):
+    try:
+        u = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return os.environ.get("LOCAL_RANK", "0")
+
+
+# ---- roofline inputs ------------------------------------------------------------------------
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1803_03922_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_bfs_level_loop_%s.txt" % workload)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---- device runs ----------------------------------------------------------------------------
+
+class DeviceWorkload:
+    def __init__(self, name, w, rank, keep_host_edges=False, th=None, stream=None):
+        import torch
+
+        import graphgen
+        import paper_1803_03922_gb300 as bfs
+
+        self.name, self.w = name, w
+        self.n = 1 << w["scale"]
+        self.th = w["th"] if th is None else th
+        src, dst = make_edges_device(w)
+        self.m = src.numel()
+        mask = graphgen.nonisolated_mask_device(self.n, src, dst).cpu().numpy()
+        self.sources = sources_for(w, mask, rank)
+        self.host_edges = (src.cpu().numpy(), dst.cpu().numpy()) if keep_host_edges else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self.g = bfs.Graph(src, dst, self.n, th=self.th, stream=stream)
+        torch.cuda.synchronize()
+        self.build_s = time.perf_counter() - t0
+        del src, dst
+        torch.cuda.empty_cache()
+        self.info = self.g.info
+        self.depth = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        # untimed pass: per-source traversal size, byte model and level log
+        self.ce, self.model, self.levels, self.dirs, self.phase = [], [], [], [], []
+        for s in self.sources:
+            _, _, st = self.g.run(int(s), self.depth, self.parent, stats=True)
+            self.ce.append(st.component_edges)
+            self.model.append(st.model_bytes)
+            self.levels.append(st.levels)
+            self.dirs.append("".join("B" if st.level[i].direction else "T" for i in range(st.logged_levels)))
+            td = bu = 0
+            for i in range(st.logged_levels):
+                lv = st.level[i]
+                dt = lv.t_end_ns - lv.t_begin_ns
+                if lv.direction:
+                    bu += dt
+                else:
+                    td += dt
+            self.phase.append((td, bu, st.device_ns))
+
+    def timed(self, steps, flush, stream):
+        """steps x len(sources) runs; returns per-run device seconds (CUDA events)."""
+        import torch
+
+        ev = []
+        for _ in range(steps):
+            for s in self.sources:
+                if flush is not None:
+                    flush.add_(1)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                self.g.run(int(s), self.depth, self.parent, stream=stream)
+                b.record(stream)
+                ev.append((a, b))
+        torch.cuda.synchronize()
+        self.g.wait(stream)
+        return [a.elapsed_time(b) / 1e3 for a, b in ev]
+
+    def gteps(self, times):
+        k = len(self.sources)
+        return [self.ce[i % k] / t / 1e9 for i, t in enumerate(times)]
+
+    def close(self):
+        self.g.close()
+
+
+def e2e_runs(dw, steps):
+    """Through the public call with pinned host result buffers: the device->host
+    copies of depth and parent are inside every timed call."""
+    import torch
+
+    import paper_1803_03922_gb300 as bfs
+
+    hd = torch.empty(dw.n, dtype=torch.int32).pin_memory()
+    hp = torch.empty(dw.n, dtype=torch.int32).pin_memory()
+    src_host = torch.tensor(dw.sources, dtype=torch.int32).pin_memory()
+    ts = []
+    for _ in range(steps):
+        for i in range(len(dw.sources)):
+            t0 = time.perf_counter()
+            bfs.bfs_run(dw.g.handle, int(src_host[i]), hd, hp)
+            ts.append(time.perf_counter() - t0)
+    k = len(dw.sources)
+    vals = [dw.ce[i % k] / t / 1e9 for i, t in enumerate(ts)]
+    return hmean(vals), ts
+
+
+def cpu_oracle_sample(w, host_edges, sources, ce_dev, budget_s=20.0, max_sources=8):
+    """The CPU oracle as it stands, single-threaded, on the same graph: a few of the
+    same sources, as many as fit the time budget."""
+    import oracle
+
+    src, dst = host_edges if host_edges is not None else make_edges_host(w)
+    t0 = time.perf_counter()
+    og = oracle.Graph(1 << w["scale"], src, dst)
+    build_s = time.perf_counter() - t0
+    vals, used, spent = [], 0, 0.0
+    for s in sources[:max_sources]:
+        t0 = time.perf_counter()
+        d, _ = og.bfs(int(s))
+        dt = time.perf_counter() - t0
+        ce = og.component_edges(d)
+        vals.append(ce / dt / 1e9)
+        used += 1
+        spent += dt
+        if spent > budget_s:
+            break
+    og.close()
+    return {"value": hmean(vals), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": "%d of the %d sources on the same graph (single-threaded C, -O2; host graph build "
+                      "%.1f s untimed)" % (used, len(sources), build_s),
+            "seconds": spent}
+
+
+# ---- main arms ------------------------------------------------------------------------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, w, ws, rank):
+    """CPU oracle arm: each step is one BFS of the oracle from one of the same
+    seeded sources (a bounded sample of the workload)."""
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+
+    src, dst = make_edges_host(w)
+    n = 1 << w["scale"]
+    mask = graphgen.nonisolated_mask_host(n, src, dst)
+    sources = sources_for(w, mask, 0)
+    og = oracle.Graph(n, src, dst)
+    del src, dst
+    k = len(sources)
+    for i in range(args.warmup):
+        og.bfs(int(sources[i % k]))
+    ts, vals = [], []
+    for i in range(args.steps):
+        s = int(sources[(args.warmup + i) % k])
+        t0 = time.perf_counter()
+        d, _ = og.bfs(s)
+        dt = time.perf_counter() - t0
+        ts.append(dt)
+        vals.append(og.component_edges(d) / dt / 1e9)
+    v = hmean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded RMAT, Graph500 parameters)",
+        "config": config_of(args.workload, w),
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "GTEPS",
+                         "sample": "one of the 64 seeded sources per step on the same graph "
+                                   "(single-threaded C, -O2)"},
+        "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, w, info=None):
+    c = {"workload": name, "graph": "RMAT" if w["kind"] == "rmat" else "Erdos-Renyi", "scale": w["scale"],
+         "n": 1 << w["scale"], "th": w["th"], "alpha": 15, "beta": 18, "sources": N_SOURCES,
+         "graph_seed": w["seed"], "source_seed": w["src_seed"],
+         "l2": "inputs larger than L2 and L2 flushed (256 MiB write) before every timed run"}
+    if w["kind"] == "rmat":
+        c.update(edge_factor=16, abcd=[0.57, 0.19, 0.19, 0.05])
+    else:
+        c.update(avg_degree=w["avgdeg"])
+    if info is not None:
+        c.update(nnz=info.nnz, delegates=info.delegates, nonisolated=info.n_nonisolated,
+                 adjacency_bytes=info.nnz * 4 + (info.n_nonisolated + 1) * 8)
+    return c
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extras", action="store_true", help="skip the TH sweep and the scale-26 graphs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w, ws, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    dw = DeviceWorkload(args.workload, w, rank, keep_host_edges=(rank == 0 and ws == 1 and not args.no_cpu))
+    log("[bench] %s: n=%d nnz=%d d=%d build %.2fs, levels %s" % (
+        args.workload, dw.n, dw.info.nnz, dw.info.delegates, dw.build_s, sorted(set(dw.levels))))
+    dw.timed(args.warmup, flush, stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    sampler = ClockSampler(gpu_id_for_smi(torch))
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    times = dw.timed(args.steps, flush, stream)
+    t_all1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    wall = t_all0.elapsed_time(t_all1) / 1e3
+    run_s = sum(times)
+    if ws > 1:
+        t = torch.tensor([run_s, wall], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        run_max, wall = float(t[0]), float(t[1])
+        edges = torch.tensor([float(sum(dw.ce) * args.steps)], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(edges)
+        value = float(edges[0]) / run_max / 1e9
+    else:
+        value = hmean(dw.gteps(times))
+    k = len(dw.sources)
+    model_total = sum(dw.model[i % k] for i in range(len(times)))
+    achieved = model_total / run_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    e2e_val, e2e_ts = e2e_runs(dw, max(1, min(args.steps, 3)))
+    td_ns = sum(p[0] for p in dw.phase)
+    bu_ns = sum(p[1] for p in dw.phase)
+    dev_ns = sum(p[2] for p in dw.phase)
+    paper_style = gmean([(16 << w["scale"]) / t / 1e9 for i, t in enumerate(times) if dw.levels[i % k] > 2])
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * run_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded RMAT, Graph500 parameters)",
+        "config": dict(config_of(args.workload, w, dw.info),
+                       parallelism="replicas" if ws > 1 else "single GPU"),
+        "gpu_launches": len(times),
+        "clocks": clocks,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
+                     "kernel": "bfs_level_loop", "peak_kind": peak_kind,
+                     "model_bytes_per_launch": model_total / len(times)},
+        "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
+                "d2h_bytes_per_step": 8 * dw.n * k},
+        "detail": {"wall_ms_per_step_with_flush": 1e3 * wall / args.steps,
+                   "gteps_aggregate": sum(dw.ce[i % k] for i in range(len(times))) / run_s / 1e9,
+                   "gteps_paper_style_geomean": paper_style,
+                   "ms_per_bfs_median": 1e3 * statistics.median(times),
+                   "build_s": dw.build_s, "levels": statistics.median(dw.levels),
+                   "directions_first_source": dw.dirs[0],
+                   "forward_share": td_ns / dev_ns if dev_ns else None,
+                   "backward_share": bu_ns / dev_ns if dev_ns else None,
+                   "e2e_ms_per_bfs_median": 1e3 * statistics.median(e2e_ts)},
+    }
+    host_edges = dw.host_edges
+    sources = dw.sources
+    ce_dev = dw.ce
+    dw.close()
+    del dw
+
+    if rank == 0 and not args.no_extras:
+        extras = {}
+        for th in (32, 128, 256):
+            if args.workload != "rmat22":
+                break
+            d2 = DeviceWorkload("rmat22", w, rank, th=th)
+            t2 = d2.timed(1, flush, stream)
+            extras["rmat22_th%d" % th] = {"gteps": hmean(d2.gteps(t2)), "delegates": d2.info.delegates,
+                                          "roofline_frac": sum(d2.model) / sum(t2) / 1e9 / peak}
+            d2.close()
+        for name in ("rmat26", "er26"):
+            try:
+                d3 = DeviceWorkload(name, WORKLOADS[name], rank)
+                d3.timed(1, None, stream)
+                t3 = d3.timed(2, None, stream)
+                extras[name] = {"gteps": hmean(d3.gteps(t3)), "ms_per_bfs_median": 1e3 * statistics.median(t3),
+                                "roofline_frac": sum(d3.model[i % len(d3.sources)] for i in range(len(t3)))
+                                / sum(t3) / 1e9 / peak,
+                                "nnz": d3.info.nnz, "delegates": d3.info.delegates,
+                                "levels": statistics.median(d3.levels), "build_s": d3.build_s,
+                                "directions_first_source": d3.dirs[0]}
+                d3.close()
+                del d3
+                torch.cuda.empty_cache()
+            except Exception as e:  # report, do not hide
+                extras[name] = {"error": str(e)}
+        line["extras"] = extras
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(w, host_edges, sources, ce_dev)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

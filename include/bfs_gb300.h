@@ -63,7 +63,7 @@ typedef struct bfs_options {
   int32_t beta;             /* Beamer beta (default 18) */
   double factor0;           /* BFS_SCHED_PAPER: forward->backward when FV > factor0 * BV (default 0.5) */
   double factor1;           /* BFS_SCHED_PAPER: backward->forward when FV < factor1 * BV (default 1e-7) */
-  int32_t td_parent;        /* BFS_TD_PARENT_* (default PULL) */
+  int32_t td_parent;        /* BFS_TD_PARENT_* (default ATOMICMIN) */
   int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM (0 = as many as fit) */
   int32_t barrier_timeout_ms; /* bound of every device-side grid-barrier wait (default 2000) */
   int32_t test_skip_barrier;  /* testing only: CTA 0 leaves before the first grid barrier, so the
@@ -73,7 +73,7 @@ typedef struct bfs_options {
 } bfs_options;
 
 /* Fills *opt with the defaults: th 64, host edges, Beamer alpha 15 / beta 18,
- * paper factors 0.5 / 1e-7, PULL parents, 2000 ms barrier bound. */
+ * paper factors 0.5 / 1e-7, atomicMin parents, 2000 ms barrier bound, 60 s run bound. */
 int bfs_options_default(bfs_options* opt);
 
 typedef struct bfs_graph bfs_graph;

@@ -222,7 +222,7 @@ class Graph:
         opt.th = th
         for k, v in options.items():
             setattr(opt, k, v)
-        self.options = dict(options)
+        self.opt = opt
         self._h = bfs_build_graph(src, dst, num_vertices, opt, stream)
         self.info = bfs_graph_get_info(self._h)
         self.n = self.info.n
@@ -236,7 +236,8 @@ class Graph:
         for k, v in options.items():
             setattr(opt, k, v)
         bfs_set_options(self._h, opt)
-        self.options = dict(options)
+        opt.th, opt.edges_on_device = self.opt.th, self.opt.edges_on_device
+        self.opt = opt
 
     def export(self):
         return bfs_graph_export(self._h)

@@ -160,7 +160,7 @@ extern "C" int bfs_options_default(bfs_options* opt) {
   opt->beta = 18;
   opt->factor0 = 0.5;
   opt->factor1 = 1e-7;
-  opt->td_parent = BFS_TD_PARENT_PULL;
+  opt->td_parent = BFS_TD_PARENT_ATOMICMIN;
   opt->blocks_per_sm = 0;
   opt->barrier_timeout_ms = 2000;
   opt->run_timeout_ms = 60000;

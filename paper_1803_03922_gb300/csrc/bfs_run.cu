@@ -7,17 +7,19 @@
 //     warp gathers the 32 rows' entries together); delegates of F_L come from a
 //     list of 512-entry row chunks, so a very high-degree row is spread over many
 //     warps (merge-style partitioning, Sec. IV-A) and read with 128-bit loads.
-//     Every unvisited target sets its bit in the discovered bitmap N; the lane
-//     whose atomicOr set the bit appends it to the next queue or chunk list.
+//     Every unvisited target sets its bit in the discovered bitmap N, and (the
+//     default) offers the frontier vertex's caller id to its parent by atomicMin.
 //   backward (bottom-up, pull; Sec. II-C, IV-B): every unvisited non-isolated
 //     vertex scans its row, which is sorted by caller id, and stops at the first
 //     neighbour already visited; that neighbour is the canonical parent.
 //   level end (fused): N is merged into the visited bitmap V; after a forward
-//     level the parent of each newly reached vertex is picked by the same
-//     first-hit scan over its sorted row (predicate: visited before this level).
+//     level the same pass converts N into the next queue and chunk list, writes
+//     the depths and counts the new frontier.
 //   direction (Sec. IV-B): chosen from the frontier counters by every CTA alike.
 // When a backward level is followed by a forward one, the bitmap of the new
-// frontier is converted into the queue and chunk list first.
+// frontier is converted into the queue and chunk list first.  Work is assigned
+// statically (warp w takes items w, w + warps, ...) and counters are added once
+// per CTA, so no single global counter is contended.
 //
 // Every grid-barrier wait is bounded by a %globaltimer deadline; on expiry the
 // kernel records BFS_ERR_TIMEOUT and every CTA returns.
@@ -110,6 +112,60 @@ struct Acc {
   unsigned long long nf = 0, mf = 0, edges = 0, scanned = 0, fix = 0;
 };
 
+// Adds every thread's Acc into global counters with one atomic per CTA and
+// counter (the targets may be null).  Called by all threads of the CTA.
+__device__ void flush_block(Acc& a, unsigned long long* nf, unsigned long long* mf, unsigned long long* edges,
+                            unsigned long long* scanned, unsigned long long* fix) {
+  __shared__ unsigned long long s_red[5];
+  if (threadIdx.x < 5) s_red[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned long long x[5] = {warp_sum(a.nf), warp_sum(a.mf), warp_sum(a.edges), warp_sum(a.scanned),
+                                   warp_sum(a.fix)};
+  if (lane_id() == 0)
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (x[i]) atomicAdd(&s_red[i], x[i]);
+  __syncthreads();
+  unsigned long long* t[5] = {nf, mf, edges, scanned, fix};
+  if (threadIdx.x < 5 && s_red[threadIdx.x] && t[threadIdx.x]) atomicAdd(t[threadIdx.x], s_red[threadIdx.x]);
+  a = Acc();
+}
+
+// Exclusive prefix sum over the CTA of two per-thread counts; returns the
+// CTA totals.  Called by all threads of the CTA.
+__device__ void block_scan2(unsigned long long a, unsigned long long b, unsigned long long& ea,
+                            unsigned long long& eb, unsigned long long& ta, unsigned long long& tb) {
+  __shared__ unsigned long long s_a[kWarpsPerBlock], s_b[kWarpsPerBlock];
+  const int lane = lane_id(), wid = threadIdx.x >> 5;
+  unsigned long long ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long xa = __shfl_up_sync(kFull, ia, o), xb = __shfl_up_sync(kFull, ib, o);
+    if (lane >= o) {
+      ia += xa;
+      ib += xb;
+    }
+  }
+  if (lane == 31) {
+    s_a[wid] = ia;
+    s_b[wid] = ib;
+  }
+  __syncthreads();
+  unsigned long long pa = 0, pb = 0;
+  ta = tb = 0;
+  for (int w = 0; w < kWarpsPerBlock; ++w) {
+    if (w < wid) {
+      pa += s_a[w];
+      pb += s_b[w];
+    }
+    ta += s_a[w];
+    tb += s_b[w];
+  }
+  ea = pa + ia - a;
+  eb = pb + ib - b;
+  __syncthreads();
+}
+
 // Visited-state probe for the pull scans.  Backward: visited before this level
 // (V is read-only during the expansion).  Parent pick after a forward level:
 // visited and not discovered in this level (V is being merged concurrently; the
@@ -121,16 +177,54 @@ __device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t*
   return s;
 }
 
-// Pull scan for one vertex per lane: lanes with `act` scan [beg,end) in order and
-// stop at the first neighbour passing the probe.  The first kWin entries are read
-// by the owning lane; rows not settled by then are finished by 8-lane groups,
-// four rows at a time, one 32-byte sector per group and step.
+// Whole-warp scan of row entries [from, end) of a row starting at rbeg, 128
+// entries (one 128-bit load per lane) per step; returns the first entry passing
+// the probe (or -1) and kv = its position in the row + 1 (or end - rbeg).
+template <bool kFix>
+__device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t end,
+                         const uint32_t* __restrict__ Ncur, int64_t& kv) {
+  const int lane = lane_id();
+  for (int64_t j0 = from & ~(int64_t)3; j0 < end; j0 += 128) {
+    const int64_t j = j0 + lane * 4;
+    unsigned best = 0xFFFFFFFFu;
+    int bc = -1;
+    if (j < end) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
+      const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+      for (int t = 3; t >= 0; --t) {
+        const int64_t idx = j + t;
+        if (idx >= from && idx < end && probe<kFix>(p, cs[t], Ncur)) {
+          best = (unsigned)(idx - rbeg);
+          bc = cs[t];
+        }
+      }
+    }
+    const unsigned wbest = __reduce_min_sync(kFull, best);
+    if (wbest != 0xFFFFFFFFu) {
+      const unsigned who = __ballot_sync(kFull, best == wbest);
+      kv = (int64_t)wbest + 1;
+      return __shfl_sync(kFull, bc, __ffs(who) - 1);
+    }
+  }
+  kv = end - rbeg;
+  return -1;
+}
+
+// Pull scan, one vertex per lane: lanes with `act` scan their row [beg,end) in
+// order and stop at the first neighbour passing the probe.
+//  A: each lane reads the first kWin entries of its own row;
+//  B: rows with at most kShort entries left go to 8-lane groups, four rows at a
+//     time, one 32-byte sector per group and step;
+//  C: longer rows are finished by the whole warp, one row at a time, 128 entries
+//     per step.
 // Returns the neighbour's internal id or -1; kv = entries examined (first-hit
 // position + 1, or the degree).
 template <bool kFix>
 __device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end,
                           const uint32_t* __restrict__ Ncur, int64_t& kv) {
   constexpr int kWin = 4;
+  constexpr int64_t kShort = 64;
   const int lane = lane_id();
   int hit = -1;
   int64_t k = 0;
@@ -147,7 +241,9 @@ __device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end
       }
     if (hit < 0) k = lim - beg;
   }
-  unsigned rem = __ballot_sync(kFull, act && hit < 0 && beg + kWin < end);
+  const bool more = act && hit < 0 && beg + kWin < end;
+  const bool longrow = more && (end - beg - kWin) > kShort;
+  unsigned rem = __ballot_sync(kFull, more && !longrow);
   const int g = lane >> 3, sub = lane & 7;
   while (rem) {
     const int take = min(__popc(rem), 4);
@@ -193,101 +289,42 @@ __device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end
     }
     for (int q = 0; q < take; ++q) rem &= rem - 1;
   }
+  unsigned lrem = __ballot_sync(kFull, longrow);
+  while (lrem) {
+    const int owner = __ffs(lrem) - 1;
+    lrem &= lrem - 1;
+    const int64_t rbeg = __shfl_sync(kFull, beg, owner);
+    const int64_t rend = __shfl_sync(kFull, end, owner);
+    int64_t k2;
+    const int h2 = warp_scan<kFix>(p, rbeg, rbeg + kWin, rend, Ncur, k2);
+    if (lane == owner) {
+      hit = h2;
+      k = k2;
+    }
+  }
   kv = k;
   return hit;
 }
 
-// Pull scan of one high-degree vertex by the whole warp with 128-bit loads
-// (128 row entries per step).  Same result and kv as pull_lanes.
-template <bool kFix>
-__device__ int warp_pull(const BfsParams& p, int v, const uint32_t* __restrict__ Ncur, int64_t& kv,
-                         int64_t& deg) {
-  const int lane = lane_id();
-  const int64_t beg = p.off[v], end = p.off[v + 1];
-  deg = end - beg;
-  for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 128) {
-    const int64_t j = j0 + lane * 4;
-    unsigned best = 0xFFFFFFFFu;
-    int bc = -1;
-    if (j < end) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
-      const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-      for (int t = 3; t >= 0; --t) {
-        const int64_t idx = j + t;
-        if (idx >= beg && idx < end && probe<kFix>(p, cs[t], Ncur)) {
-          best = (unsigned)(idx - beg);
-          bc = cs[t];
-        }
-      }
-    }
-    const unsigned wbest = __reduce_min_sync(kFull, best);
-    if (wbest != 0xFFFFFFFFu) {
-      const unsigned who = __ballot_sync(kFull, best == wbest);
-      kv = (int64_t)wbest + 1;
-      return __shfl_sync(kFull, bc, __ffs(who) - 1);
-    }
-  }
-  kv = deg;
-  return -1;
-}
-
 // ---- forward level ------------------------------------------------------------------------
 
-struct TdOut {
-  uint32_t* N;   // discovered bitmap of this level
-  int32_t* Qn;   // next normal queue
-  int2* CLn;     // next delegate chunk list
-  LevelSlot* sn; // counters of the next frontier
-  int depth;     // depth of newly reached vertices
-};
-
-// One row entry u->v of a forward visit, called by all 32 lanes together
-// (v < 0: lane idle).  The lane whose atomicOr set v's bit owns v: it writes the
-// depth, adds v's degree to m_f and appends v to the next queue or chunk list.
-__device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, const TdOut& o, Acc& acc) {
-  bool win = false;
-  if (v >= 0) {
-    const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
-    if (!(p.V[w] & bit)) {
-      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
-      if (!(__ldcg(o.N + w) & bit)) win = !(atomicOr(o.N + w, bit) & bit);
-    }
-  }
-  const unsigned wb = __ballot_sync(kFull, win);
-  if (!wb) return;
-  const int lane = lane_id();
-  int64_t deg = 0;
-  if (win) {
-    deg = p.off[v + 1] - p.off[v];
-    p.depth_i[v] = o.depth;
-    acc.nf += 1;
-    acc.mf += (unsigned long long)deg;
-  }
-  const bool isn = win && v >= p.d;
-  const unsigned nb = __ballot_sync(kFull, isn);
-  if (nb) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&o.sn->qn, (unsigned long long)__popc(nb));
-    base = __shfl_sync(kFull, base, 0);
-    if (isn) o.Qn[base + __popc(nb & ((1u << lane) - 1u))] = v;
-  }
-  const bool isd = win && v < p.d;
-  if (__ballot_sync(kFull, isd)) {
-    const int64_t nch = isd ? (deg + kChunk - 1) / kChunk : 0;
-    const int64_t incl = warp_incl_scan(nch);
-    unsigned long long base = 0;
-    if (lane == 31) base = atomicAdd(&o.sn->nch, (unsigned long long)incl);
-    base = __shfl_sync(kFull, base, 31);
-    if (isd)
-      for (int64_t k = 0; k < nch; ++k) o.CLn[base + (incl - nch) + k] = make_int2(v, (int)k);
-  }
+// One row entry u->v of a forward visit (v < 0: lane idle).  An unvisited target
+// gets its bit in N (fire-and-forget atomicOr); with atomicMin parents, the
+// frontier vertex's caller id is also offered to v's parent slot.  Which lane
+// set the bit does not matter: the level end builds the next frontier from N.
+__device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, uint32_t* __restrict__ N) {
+  if (v < 0) return;
+  const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
+  if (p.V[w] & bit) return;
+  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
+  atomicOr(N + w, bit);
 }
 
 // 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
-// concatenation of the 32 rows 32 entries at a time.
+// concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
+// whose inclusive degree prefix first exceeds e).
 __device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int64_t qn, int64_t b,
-                         const TdOut& o, Acc& acc) {
+                         uint32_t* __restrict__ N) {
   const int lane = lane_id();
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
@@ -312,13 +349,12 @@ __device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int
     const int64_t ob = __shfl_sync(kFull, beg, pos);
     const int64_t ox = __shfl_sync(kFull, excl, pos);
     const int opc = __shfl_sync(kFull, pc, pos);
-    const int v = e < total ? p.col[ob + (e - ox)] : -1;
-    td_edge(p, v, opc, o, acc);
+    td_edge(p, e < total ? p.col[ob + (e - ox)] : -1, opc, N);
   }
 }
 
-// One 512-entry chunk of a delegate's row, 128-bit loads.
-__device__ void td_chunk(const BfsParams& p, int2 ck, const TdOut& o, Acc& acc) {
+// One kChunk-entry piece of a delegate's row, 128-bit loads.
+__device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) {
   const int lane = lane_id();
   const int u = ck.x;
   const int64_t rb = p.off[u], re = p.off[u + 1];
@@ -327,78 +363,44 @@ __device__ void td_chunk(const BfsParams& p, int2 ck, const TdOut& o, Acc& acc) 
   const int pc = (p.td_parent == BFS_TD_PARENT_ATOMICMIN) ? p.caller_of[u] : 0;
   for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 128) {
     const int64_t j = j0 + lane * 4;
-    int4 c4 = make_int4(-1, -1, -1, -1);
-    if (j < end) c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
-    const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int64_t idx = j + t;
-      td_edge(p, (idx >= beg && idx < end) ? cs[t] : -1, pc, o, acc);
+    if (j < end) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
+      if (j >= beg) td_edge(p, c4.x, pc, N);
+      if (j + 1 >= beg && j + 1 < end) td_edge(p, c4.y, pc, N);
+      if (j + 2 >= beg && j + 2 < end) td_edge(p, c4.z, pc, N);
+      if (j + 3 >= beg && j + 3 < end) td_edge(p, c4.w, pc, N);
     }
   }
 }
 
-__device__ __forceinline__ long long grab(unsigned long long* ctr) {
-  unsigned long long x = 0;
-  if (lane_id() == 0) x = atomicAdd(ctr, 1ull);
-  return (long long)__shfl_sync(kFull, x, 0);
-}
-
-__device__ void expand_td(const BfsParams& p, int L, Acc& acc) {
-  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+// Work items of a forward level: the delegate chunks of F_L, then the normal
+// queue in batches of 32; warp w takes items w, w + warps, ... (no shared counter).
+__device__ void expand_td(const BfsParams& p, int L) {
+  const LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sc->qn);
   const int64_t nch = (int64_t)__ldcg(&sc->nch);
-  const int64_t nb = (qn + 31) / 32;
+  const int64_t total = nch + (qn + 31) / 32;
   const int32_t* Qc = (L & 1) ? p.Q1 : p.Q0;
   const int2* CLc = (L & 1) ? p.CL1 : p.CL0;
-  TdOut o;
-  o.N = (L & 1) ? p.N1 : p.N0;
-  o.Qn = (L & 1) ? p.Q0 : p.Q1;
-  o.CLn = (L & 1) ? p.CL0 : p.CL1;
-  o.sn = p.slot + ((L + 1) & (kSlots - 1));
-  o.depth = L + 1;
-  const int64_t total = nch + nb;
-  for (long long it = grab(&sc->work); it < total; it = grab(&sc->work)) {
+  uint32_t* N = (L & 1) ? p.N1 : p.N0;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = gwarp; it < total; it += nwarps) {
     if (it < nch)
-      td_chunk(p, CLc[it], o, acc);
+      td_chunk(p, CLc[it], N);
     else
-      td_batch(p, Qc, qn, it - nch, o, acc);
+      td_batch(p, Qc, qn, it - nch, N);
   }
 }
 
 // ---- backward level -----------------------------------------------------------------------
 
-// Unvisited vertices of one 32-vertex word; returns the mask of those that found
-// a parent.  Delegates (high degree) are scanned by the whole warp, normal
-// vertices by pull_lanes.
+// Unvisited vertices of one 32-vertex word (mask m); returns the mask of those
+// that found a parent, after writing their depth and parent.
 __device__ unsigned bu_word(const BfsParams& p, int64_t word, unsigned m, int L, Acc& acc) {
   const int lane = lane_id();
-  const int64_t v0 = word * 32;
-  unsigned dmask = 0;
-  if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
-  unsigned found = 0;
-  unsigned md = m & dmask;
-  while (md) {
-    const int i = __ffs(md) - 1;
-    md &= md - 1;
-    const int v = (int)(v0 + i);
-    int64_t kv, deg;
-    const int hit = warp_pull<false>(p, v, nullptr, kv, deg);
-    if (lane == 0) {
-      acc.scanned += 1;
-      acc.edges += (unsigned long long)kv;
-      if (hit >= 0) {
-        p.parent_i[v] = p.caller_of[hit];
-        p.depth_i[v] = L + 1;
-        acc.nf += 1;
-        acc.mf += (unsigned long long)deg;
-      }
-    }
-    if (hit >= 0) found |= 1u << i;
-  }
-  const unsigned mn = m & ~dmask;
-  const bool act = (mn >> lane) & 1u;
-  const int v = (int)(v0 + lane);
+  const bool act = (m >> lane) & 1u;
+  const int v = (int)(word * 32 + lane);
   int64_t beg = 0, end = 0;
   if (act) {
     beg = p.off[v];
@@ -416,21 +418,23 @@ __device__ unsigned bu_word(const BfsParams& p, int64_t word, unsigned m, int L,
       acc.mf += (unsigned long long)(end - beg);
     }
   }
-  found |= __ballot_sync(kFull, act && hit >= 0);
-  return found;
+  return __ballot_sync(kFull, act && hit >= 0);
 }
 
+// Items of 8 bitmap words (256 vertices); warp w takes items w, w + warps, ...
 __device__ void expand_bu(const BfsParams& p, int L, Acc& acc) {
-  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  constexpr int kItemWords = 8;
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
   const int64_t W = p.words;
-  const int64_t groups = (W + 31) / 32;
+  const int64_t items = (W + kItemWords - 1) / kItemWords;
   const int tail = p.n_ni & 31;
-  for (long long gi = grab(&sc->work); gi < groups; gi = grab(&sc->work)) {
-    const int64_t w = gi * 32 + lane;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = gwarp; it < items; it += nwarps) {
+    const int64_t w = it * kItemWords + lane;
     unsigned vis = kFull;
-    if (w < W) {
+    if (lane < kItemWords && w < W) {
       vis = p.V[w];
       if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
     }
@@ -440,115 +444,126 @@ __device__ void expand_bu(const BfsParams& p, int L, Acc& acc) {
       const int j = __ffs(pend) - 1;
       pend &= pend - 1;
       const unsigned m = __shfl_sync(kFull, unv, j);
-      const unsigned f = bu_word(p, gi * 32 + j, m, L, acc);
-      if (lane == 0 && f) N[gi * 32 + j] = f;
+      const unsigned f = bu_word(p, it * kItemWords + j, m, L, acc);
+      if (lane == 0 && f) N[it * kItemWords + j] = f;
     }
   }
 }
 
-// ---- level end and conversions -------------------------------------------------------------
+// ---- bitmap -> frontier queues --------------------------------------------------------------
 
-// Merge N into V and clear the other N buffer; after a forward level with PULL
-// parents, pick each new vertex's parent by a first-hit scan of its sorted row.
-__device__ void level_end(const BfsParams& p, int L, bool td, Acc& acc) {
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
-  uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
-  for (int64_t w = gtid; w < p.words; w += gthreads) {
-    const unsigned nb = __ldcg(Ncur + w);
-    if (nb) p.V[w] |= nb;
-    Noth[w] = 0;
-  }
-  if (td && p.td_parent == BFS_TD_PARENT_PULL) {
-    const LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
-    const int64_t qn = (int64_t)__ldcg(&sn->qn);
-    const int64_t nch = (int64_t)__ldcg(&sn->nch);
-    const int32_t* Qn = (L & 1) ? p.Q0 : p.Q1;
-    const int2* CLn = (L & 1) ? p.CL0 : p.CL1;
-    const int lane = lane_id();
-    const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
-    for (int64_t b = gwarp; b * 32 < qn; b += nwarps) {
-      const int64_t i = b * 32 + lane;
-      const bool act = i < qn;
-      const int v = act ? Qn[i] : 0;
-      int64_t beg = 0, end = 0;
-      if (act) {
-        beg = p.off[v];
-        end = p.off[v + 1];
-      }
-      int64_t kv = 0;
-      const int hit = pull_lanes<true>(p, act, beg, end, Ncur, kv);
-      if (act) {
-        acc.fix += (unsigned long long)kv;
-        if (hit >= 0) p.parent_i[v] = p.caller_of[hit];
+// Reads the discovered bitmap Nsrc of a level and writes the next frontier as a
+// normal-vertex queue Q and a delegate chunk list CL, reserving their ranges
+// with one atomic per CTA and step.  With `merge`, also ORs Nsrc into V and
+// clears Nclr.  With `count` (after a forward level), also writes depth `depth`
+// for every new vertex and adds n_f and m_f.  Called by all threads.
+__device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
+                                     int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* slot, bool merge,
+                                     bool count, int depth, Acc& acc) {
+  __shared__ unsigned long long s_base[2];
+  const int64_t W = p.words;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < W; w0 += stride) {
+    const int64_t w = w0 + threadIdx.x;
+    unsigned nb = 0;
+    if (w < W) {
+      nb = __ldcg(Nsrc + w);
+      if (merge) {
+        if (nb) p.V[w] |= nb;
+        Nclr[w] = 0u;
       }
     }
-    for (int64_t e = gwarp; e < nch; e += nwarps) {
-      const int2 ck = CLn[e];
-      if (ck.y != 0) continue;
-      int64_t kv, deg;
-      const int hit = warp_pull<true>(p, ck.x, Ncur, kv, deg);
-      if (lane == 0) {
-        acc.fix += (unsigned long long)kv;
-        if (hit >= 0) p.parent_i[ck.x] = p.caller_of[hit];
-      }
-    }
-  }
-}
-
-// Frontier F_L held as the bitmap of level L-1's discoveries -> queue + chunk list.
-__device__ void convert_to_queues(const BfsParams& p, int L) {
-  const uint32_t* Nf = (L & 1) ? p.N0 : p.N1;  // discoveries of level L-1
-  int32_t* Q = (L & 1) ? p.Q1 : p.Q0;
-  int2* CL = (L & 1) ? p.CL1 : p.CL0;
-  LevelSlot* sc = p.slot + (L & (kSlots - 1));
-  const int lane = lane_id();
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  const int64_t Wr = (p.words + 31) & ~(int64_t)31;  // warp-uniform trip count
-  for (int64_t w = gtid; w < Wr; w += gthreads) {
-    const unsigned nb = w < p.words ? __ldcg(Nf + w) : 0u;
     const int64_t v0 = w * 32;
     unsigned dmask = 0;
     if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
     const unsigned nn = nb & ~dmask;
-    const int64_t cnt = __popc(nn);
-    const int64_t incl = warp_incl_scan(cnt);
-    unsigned long long base = 0;
-    if (lane == 31 && incl) base = atomicAdd(&sc->qn, (unsigned long long)incl);
-    base = __shfl_sync(kFull, base, 31) + (incl - cnt);
+    unsigned long long nchunks = 0;
+    if (count) {
+      unsigned x = nb;
+      while (x) {
+        const int i = __ffs(x) - 1;
+        x &= x - 1;
+        const int v = (int)(v0 + i);
+        const int64_t deg = p.off[v + 1] - p.off[v];
+        p.depth_i[v] = depth;
+        acc.nf += 1;
+        acc.mf += (unsigned long long)deg;
+        if (v < p.d) nchunks += (unsigned long long)((deg + kChunk - 1) / kChunk);
+      }
+    } else {
+      unsigned x = nb & dmask;
+      while (x) {
+        const int i = __ffs(x) - 1;
+        x &= x - 1;
+        const int v = (int)(v0 + i);
+        nchunks += (unsigned long long)((p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk);
+      }
+    }
+    unsigned long long eq, ec, tq, tc;
+    block_scan2((unsigned long long)__popc(nn), nchunks, eq, ec, tq, tc);
+    if (threadIdx.x == 0) {
+      s_base[0] = tq ? atomicAdd(&slot->qn, tq) : 0ull;
+      s_base[1] = tc ? atomicAdd(&slot->nch, tc) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long qb = s_base[0] + eq, cb = s_base[1] + ec;
+    __syncthreads();
     unsigned x = nn;
     while (x) {
       const int i = __ffs(x) - 1;
       x &= x - 1;
-      Q[base++] = (int)(v0 + i);
+      Q[qb++] = (int)(v0 + i);
     }
-    unsigned dd = nb & dmask;
-    while (dd) {
-      const int i = __ffs(dd) - 1;
-      dd &= dd - 1;
+    x = nb & dmask;
+    while (x) {
+      const int i = __ffs(x) - 1;
+      x &= x - 1;
       const int v = (int)(v0 + i);
-      const int64_t deg = p.off[v + 1] - p.off[v];
-      const int64_t nch = (deg + kChunk - 1) / kChunk;
-      const unsigned long long b = atomicAdd(&sc->nch, (unsigned long long)nch);
-      for (int64_t k = 0; k < nch; ++k) CL[b + k] = make_int2(v, (int)k);
+      const int64_t nc = (p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk;
+      for (int64_t k = 0; k < nc; ++k) CL[cb++] = make_int2(v, (int)k);
     }
   }
 }
 
-__device__ void flush_acc(Acc& a, unsigned long long* nf, unsigned long long* mf, unsigned long long* edges,
-                          unsigned long long* scanned, unsigned long long* fix) {
-  const unsigned long long x0 = warp_sum(a.nf), x1 = warp_sum(a.mf), x2 = warp_sum(a.edges),
-                           x3 = warp_sum(a.scanned), x4 = warp_sum(a.fix);
-  if (lane_id() == 0) {
-    if (x0 && nf) atomicAdd(nf, x0);
-    if (x1 && mf) atomicAdd(mf, x1);
-    if (x2 && edges) atomicAdd(edges, x2);
-    if (x3 && scanned) atomicAdd(scanned, x3);
-    if (x4 && fix) atomicAdd(fix, x4);
+// Canonical parents of the vertices found by a forward level, by a first-hit
+// scan of their sorted rows (the PULL option).
+__device__ void pull_parents(const BfsParams& p, int L, Acc& acc) {
+  uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+  const LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
+  const int64_t qn = (int64_t)__ldcg(&sn->qn);
+  const int64_t nch = (int64_t)__ldcg(&sn->nch);
+  const int32_t* Qn = (L & 1) ? p.Q0 : p.Q1;
+  const int2* CLn = (L & 1) ? p.CL0 : p.CL1;
+  const int lane = lane_id();
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = gwarp; b * 32 < qn; b += nwarps) {
+    const int64_t i = b * 32 + lane;
+    const bool act = i < qn;
+    const int v = act ? Qn[i] : 0;
+    int64_t beg = 0, end = 0;
+    if (act) {
+      beg = p.off[v];
+      end = p.off[v + 1];
+    }
+    int64_t kv = 0;
+    const int hit = pull_lanes<true>(p, act, beg, end, Ncur, kv);
+    if (act) {
+      acc.fix += (unsigned long long)kv;
+      if (hit >= 0) p.parent_i[v] = p.caller_of[hit];
+    }
   }
-  a = Acc();
+  for (int64_t e = gwarp; e < nch; e += nwarps) {
+    const int2 ck = CLn[e];
+    if (ck.y != 0) continue;
+    const int64_t rb = p.off[ck.x], re = p.off[ck.x + 1];
+    int64_t kv;
+    const int hit = warp_scan<true>(p, rb, rb, re, Ncur, kv);
+    if (lane == 0) {
+      acc.fix += (unsigned long long)kv;
+      if (hit >= 0) p.parent_i[ck.x] = p.caller_of[hit];
+    }
+  }
 }
 
 // Direction of level L+1 from its frontier (Sec. IV-B), computed alike by every CTA.
@@ -662,24 +677,42 @@ __device__ void run_body(const BfsParams& p) {
     if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
       set_failed(p, BFS_ERR_TIMEOUT);
     const int dir = s_dir;
+    LevelSlot* sc = p.slot + (L & (kSlots - 1));
+    LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
+    uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+    uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
     if (s_conv) {
-      convert_to_queues(p, L);
+      // F_L is the bitmap of the previous (backward) level's discoveries.
+      frontier_from_bitmap(p, Noth, nullptr, (L & 1) ? p.Q1 : p.Q0, (L & 1) ? p.CL1 : p.CL0, sc, false, false, 0,
+                           acc);
       if (!grid_sync(p)) return;
     }
     if (leader) s_tb = gtimer();
-    LevelSlot* sc = p.slot + (L & (kSlots - 1));
-    LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
     if (dir == 0) {
-      expand_td(p, L, acc);
-      flush_acc(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+      expand_td(p, L);
     } else {
       expand_bu(p, L, acc);
-      flush_acc(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
+      flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
     }
     if (!grid_sync(p)) return;
     if (leader) s_te = gtimer();
-    level_end(p, L, dir == 0, acc);
-    flush_acc(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+    if (dir == 0) {
+      // merge, then the next frontier's queues, depths and counts
+      frontier_from_bitmap(p, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true, true, L + 1,
+                           acc);
+      flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+      if (p.td_parent == BFS_TD_PARENT_PULL) {
+        if (!grid_sync(p)) return;  // the queues of F_{L+1} are complete
+        pull_parents(p, L, acc);
+        flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+      }
+    } else {
+      for (int64_t w = gtid; w < p.words; w += gthreads) {
+        const unsigned nb = __ldcg(Ncur + w);
+        if (nb) p.V[w] |= nb;
+        Noth[w] = 0u;
+      }
+    }
     if (leader) p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
     if (!grid_sync(p)) return;
     if (threadIdx.x == 0) {
@@ -737,6 +770,7 @@ __device__ void run_body(const BfsParams& p) {
     p.hdr->reached = src_in ? s_reach_v : 1;
   }
 }
+
 
 }  // namespace
 

@@ -60,7 +60,7 @@ def check_against_oracle(og: oracle.Graph, g, sources, stats=False, th=None):
             assert st.component_edges == og.component_edges(want_d)
             assert st.reached == int((want_d >= 0).sum())
             if th is not None:
-                check_counters(og, s, want_d, st, th, pull=g.options.get("td_parent", 0) == 0)
+                check_counters(og, s, want_d, st, th, pull=g.opt.td_parent == 0)
 
 
 def check_counters(og, s, depth, st, th, pull=True):
