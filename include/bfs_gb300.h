@@ -141,7 +141,9 @@ typedef struct bfs_stats {
   int64_t component_edges; /* unique undirected edges in the traversed component (GTEPS numerator) */
   int64_t edges_examined;  /* sum over levels */
   int64_t model_bytes;     /* algorithmic HBM bytes of this run (byte model of the design notes) */
-  uint64_t device_ns;      /* %globaltimer span of the level loop */
+  uint64_t device_ns;      /* %globaltimer span of the whole run (set-up, levels, results) */
+  uint64_t setup_ns;       /* part of device_ns spent clearing state before level 0 */
+  uint64_t result_ns;      /* part of device_ns spent writing the caller-indexed results */
   bfs_level_log level[BFS_LOG_LEVELS];
 } bfs_stats;
 

@@ -63,7 +63,8 @@ class bfs_level_log(ctypes.Structure):
 
 class bfs_stats(ctypes.Structure):
     _fields_ = [("levels", c_i32), ("logged_levels", c_i32), ("reached", c_i64), ("component_edges", c_i64),
-                ("edges_examined", c_i64), ("model_bytes", c_i64), ("device_ns", c_u64),
+                ("edges_examined", c_i64), ("model_bytes", c_i64), ("device_ns", c_u64), ("setup_ns", c_u64),
+                ("result_ns", c_u64),
                 ("level", bfs_level_log * BFS_LOG_LEVELS)]
 
 
@@ -272,7 +273,7 @@ class Graph:
 
 def stats_to_dict(st: bfs_stats) -> dict:
     out = {k: getattr(st, k) for k in ("levels", "logged_levels", "reached", "component_edges",
-                                       "edges_examined", "model_bytes", "device_ns")}
+                                       "edges_examined", "model_bytes", "device_ns", "setup_ns", "result_ns")}
     out["level"] = [{f: getattr(st.level[i], f) for f, _ in bfs_level_log._fields_}
                     for i in range(st.logged_levels)]
     return out

@@ -76,7 +76,7 @@ int alloc_run_state(bfs_graph* g) {
   if ((rc = dmalloc(&g->N0, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->N1, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->depth_i, (size_t)g->n_ni + 1, &t, "alloc depth"))) return rc;
-  if ((rc = dmalloc(&g->parent_i, (size_t)g->n_ni + 1, &t, "alloc parent"))) return rc;
+  if ((rc = dmalloc(&g->parent_i, (size_t)g->n_ni + 8, &t, "alloc parent"))) return rc;
   if ((rc = dmalloc(&g->Q0, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
   if ((rc = dmalloc(&g->Q1, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
   if ((rc = dmalloc(&g->CL0, (size_t)g->cl_cap, &t, "alloc chunk list"))) return rc;
@@ -251,6 +251,8 @@ static int fill_stats(bfs_graph* g, bfs_stats* st, const RunHeader& h) {
   st->reached = (int64_t)h.reached;
   st->component_edges = (int64_t)(h.reached_edges / 2);
   st->device_ns = h.t1 - h.t0;
+  st->setup_ns = h.t_init - h.t0;
+  st->result_ns = h.t1 - h.t_loop;
   if (st->logged_levels > 0) {
     LevelLogDev lg[BFS_LOG_LEVELS];
     cudaError_t e = cudaMemcpy(lg, g->log, sizeof(LevelLogDev) * st->logged_levels, cudaMemcpyDeviceToHost);

@@ -43,6 +43,7 @@ struct RunHeader {
   int levels;          // max depth + 1
   int levels_run;      // levels executed by the loop (0 for an isolated source)
   unsigned long long t0, t1;
+  unsigned long long t_init, t_loop;  // end of the set-up, end of the level loop
   unsigned long long reached_edges;  // sum of m_f over all levels (= 2 x component edges)
   unsigned long long reached;        // sum of n_f over all levels
 };
@@ -80,6 +81,7 @@ struct BfsParams {
   unsigned int epoch;        // run number; tags the status word
   int32_t test_skip_barrier; // testing only: CTA 0 skips the first barrier
   unsigned long long run_timeout_ns;
+  int32_t out_vec4;          // out_depth/out_parent are 16-byte aligned
 };
 
 }  // namespace bfsgb

@@ -320,6 +320,20 @@ __device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, 
   atomicOr(N + w, bit);
 }
 
+// Four row entries of one lane: the four visited-bit probes are issued before
+// any reduction, so they are in flight together.
+__device__ __forceinline__ void td_edge4(const BfsParams& p, const int (&v)[4], int pcaller, uint32_t* __restrict__ N) {
+  unsigned vw[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? p.V[(unsigned)v[t] >> 5] : kFull;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
+    if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], pcaller);
+    atomicOr(N + ((unsigned)v[t] >> 5), 1u << (v[t] & 31));
+  }
+}
+
 // 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
 // concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
 // whose inclusive degree prefix first exceeds e).
@@ -365,10 +379,9 @@ __device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) 
     const int64_t j = j0 + lane * 4;
     if (j < end) {
       const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
-      if (j >= beg) td_edge(p, c4.x, pc, N);
-      if (j + 1 >= beg && j + 1 < end) td_edge(p, c4.y, pc, N);
-      if (j + 2 >= beg && j + 2 < end) td_edge(p, c4.z, pc, N);
-      if (j + 3 >= beg && j + 3 < end) td_edge(p, c4.w, pc, N);
+      const int v[4] = {j >= beg ? c4.x : -1, (j + 1 >= beg && j + 1 < end) ? c4.y : -1,
+                        (j + 2 >= beg && j + 2 < end) ? c4.z : -1, (j + 3 >= beg && j + 3 < end) ? c4.w : -1};
+      td_edge4(p, v, pc, N);
     }
   }
 }
@@ -395,57 +408,85 @@ __device__ void expand_td(const BfsParams& p, int L) {
 
 // ---- backward level -----------------------------------------------------------------------
 
-// Unvisited vertices of one 32-vertex word (mask m); returns the mask of those
-// that found a parent, after writing their depth and parent.
-__device__ unsigned bu_word(const BfsParams& p, int64_t word, unsigned m, int L, Acc& acc) {
-  const int lane = lane_id();
-  const bool act = (m >> lane) & 1u;
-  const int v = (int)(word * 32 + lane);
-  int64_t beg = 0, end = 0;
-  if (act) {
-    beg = p.off[v];
-    end = p.off[v + 1];
-  }
-  int64_t kv = 0;
-  const int hit = pull_lanes<false>(p, act, beg, end, nullptr, kv);
-  if (act) {
-    acc.scanned += 1;
-    acc.edges += (unsigned long long)kv;
-    if (hit >= 0) {
-      p.parent_i[v] = p.caller_of[hit];
-      p.depth_i[v] = L + 1;
-      acc.nf += 1;
-      acc.mf += (unsigned long long)(end - beg);
+// Position of the r-th (0-based) set bit of m; r < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));
+    if (r >= c) {
+      r -= c;
+      m >>= s;
+      pos += s;
     }
   }
-  return __ballot_sync(kFull, act && hit >= 0);
+  return pos;
 }
 
-// Items of 8 bitmap words (256 vertices); warp w takes items w, w + warps, ...
-__device__ void expand_bu(const BfsParams& p, int L, Acc& acc) {
-  constexpr int kItemWords = 8;
+// Items of iw bitmap words (iw = 4..32, larger when few vertices are left);
+// warp w takes items w, w + warps, ...  The unvisited vertices of an item are
+// gathered 32 at a time (lane i takes the i-th one), so a sparse item costs one
+// batch, not one pass per word.  A vertex that finds its parent gets depth,
+// parent and its bit in N.
+__device__ void expand_bu(const BfsParams& p, int L, long long unvisited, Acc& acc) {
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
   const int64_t W = p.words;
-  const int64_t items = (W + kItemWords - 1) / kItemWords;
+  // about 64 unvisited vertices per item: iw ~ 2 n_ni / unvisited words
+  int iw = 4;
+  while (iw < 32 && (long long)iw * unvisited < 2LL * p.n_ni) iw <<= 1;
+  const int64_t items = (W + iw - 1) / iw;
   const int tail = p.n_ni & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = gwarp; it < items; it += nwarps) {
-    const int64_t w = it * kItemWords + lane;
+    const int64_t w = it * iw + lane;
     unsigned vis = kFull;
-    if (lane < kItemWords && w < W) {
+    if (lane < iw && w < W) {
       vis = p.V[w];
       if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
     }
     const unsigned unv = ~vis;
-    unsigned pend = __ballot_sync(kFull, unv != 0);
-    while (pend) {
-      const int j = __ffs(pend) - 1;
-      pend &= pend - 1;
+    const int cnt = __popc(unv);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    for (int b = 0; b < total; b += 32) {
+      const int k = b + lane;
+      const bool act = k < total;
+      int j = 0;  // word of the k-th unvisited vertex: first lane whose prefix exceeds k
+#pragma unroll
+      for (int s = 16; s >= 1; s >>= 1) {
+        const int t = __shfl_sync(kFull, incl, j + s - 1);
+        if (t <= k) j += s;
+      }
       const unsigned m = __shfl_sync(kFull, unv, j);
-      const unsigned f = bu_word(p, it * kItemWords + j, m, L, acc);
-      if (lane == 0 && f) N[it * kItemWords + j] = f;
+      const int ex = __shfl_sync(kFull, incl - cnt, j);
+      const int bit = act ? nth_set_bit(m, k - ex) : 0;
+      const int64_t word = it * iw + j;
+      const int v = (int)(word * 32 + bit);
+      int64_t beg = 0, end = 0;
+      if (act) {
+        beg = p.off[v];
+        end = p.off[v + 1];
+      }
+      int64_t kv = 0;
+      const int hit = pull_lanes<false>(p, act, beg, end, nullptr, kv);
+      if (act) {
+        acc.scanned += 1;
+        acc.edges += (unsigned long long)kv;
+        if (hit >= 0) {
+          p.parent_i[v] = p.caller_of[hit];
+          p.depth_i[v] = L + 1;
+          atomicOr(N + word, 1u << bit);
+          acc.nf += 1;
+          acc.mf += (unsigned long long)(end - beg);
+        }
+      }
     }
   }
 }
@@ -453,18 +494,24 @@ __device__ void expand_bu(const BfsParams& p, int L, Acc& acc) {
 // ---- bitmap -> frontier queues --------------------------------------------------------------
 
 // Reads the discovered bitmap Nsrc of a level and writes the next frontier as a
-// normal-vertex queue Q and a delegate chunk list CL, reserving their ranges
-// with one atomic per CTA and step.  With `merge`, also ORs Nsrc into V and
-// clears Nclr.  With `count` (after a forward level), also writes depth `depth`
-// for every new vertex and adds n_f and m_f.  Called by all threads.
+// normal-vertex queue Q and a delegate chunk list CL.  The bitmap is cut into
+// tiles of one word per thread; a CTA scans its tile's bit counts, reserves the
+// tile's queue range with one atomic, then handles the tile's new vertices one
+// per thread (k-th set bit -> word by binary search over the prefix, bit by
+// rank).  With `merge`, also ORs Nsrc into V and clears Nclr.  With `count`
+// (after a forward level), also writes depth `depth` for every new vertex and
+// adds n_f and m_f.  Called by all threads.
 __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
                                      int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* slot, bool merge,
                                      bool count, int depth, Acc& acc) {
+  __shared__ unsigned s_nb[kThreads];
+  __shared__ int s_wpre[kThreads];
+  __shared__ int s_npre[kThreads];
   __shared__ unsigned long long s_base[2];
   const int64_t W = p.words;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x; w0 < W; w0 += stride) {
-    const int64_t w = w0 + threadIdx.x;
+  const int tid = threadIdx.x;
+  for (int64_t t0 = (int64_t)blockIdx.x * kThreads; t0 < W; t0 += (int64_t)gridDim.x * kThreads) {
+    const int64_t w = t0 + tid;
     unsigned nb = 0;
     if (w < W) {
       nb = __ldcg(Nsrc + w);
@@ -473,55 +520,79 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
         Nclr[w] = 0u;
       }
     }
+    if (!__syncthreads_or(nb != 0)) continue;
     const int64_t v0 = w * 32;
     unsigned dmask = 0;
     if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
-    const unsigned nn = nb & ~dmask;
-    unsigned long long nchunks = 0;
-    if (count) {
-      unsigned x = nb;
-      while (x) {
-        const int i = __ffs(x) - 1;
-        x &= x - 1;
-        const int v = (int)(v0 + i);
-        const int64_t deg = p.off[v + 1] - p.off[v];
+    unsigned long long ea, eb, T, Tn;
+    block_scan2((unsigned long long)__popc(nb), (unsigned long long)__popc(nb & ~dmask), ea, eb, T, Tn);
+    s_nb[tid] = nb;
+    s_wpre[tid] = (int)ea;
+    s_npre[tid] = (int)eb;
+    if (tid == 0) s_base[0] = Tn ? atomicAdd(&slot->qn, Tn) : 0ull;
+    __syncthreads();
+    const unsigned long long qbase = s_base[0];
+    const bool has_del = t0 * 32 < p.d;
+    unsigned long long nch_local = 0;
+    for (int k = tid; k < (int)T; k += kThreads) {
+      int j = 0;
+#pragma unroll
+      for (int st = kThreads / 2; st >= 1; st >>= 1)
+        if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
+      const unsigned m = s_nb[j];
+      const int bit = nth_set_bit(m, k - s_wpre[j]);
+      const int v = (int)((t0 + j) * 32 + bit);
+      const int64_t deg = p.off[v + 1] - p.off[v];
+      if (count) {
         p.depth_i[v] = depth;
         acc.nf += 1;
         acc.mf += (unsigned long long)deg;
-        if (v < p.d) nchunks += (unsigned long long)((deg + kChunk - 1) / kChunk);
       }
-    } else {
-      unsigned x = nb & dmask;
-      while (x) {
-        const int i = __ffs(x) - 1;
-        x &= x - 1;
-        const int v = (int)(v0 + i);
-        nchunks += (unsigned long long)((p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk);
+      if (v >= p.d) {
+        const int64_t jv0 = (t0 + j) * 32;
+        unsigned jd = 0;
+        if (jv0 < p.d) jd = (p.d - jv0 >= 32) ? kFull : ((1u << (p.d - jv0)) - 1u);
+        Q[qbase + s_npre[j] + __popc(m & ~jd & ((1u << bit) - 1u))] = v;
+      } else {
+        nch_local += (unsigned long long)((deg + kChunk - 1) / kChunk);
       }
     }
-    unsigned long long eq, ec, tq, tc;
-    block_scan2((unsigned long long)__popc(nn), nchunks, eq, ec, tq, tc);
-    if (threadIdx.x == 0) {
-      s_base[0] = tq ? atomicAdd(&slot->qn, tq) : 0ull;
-      s_base[1] = tc ? atomicAdd(&slot->nch, tc) : 0ull;
+    if (has_del) {
+      unsigned long long ec, dummy, tc, dummy2;
+      block_scan2(nch_local, 0ull, ec, dummy, tc, dummy2);
+      if (tid == 0) s_base[1] = tc ? atomicAdd(&slot->nch, tc) : 0ull;
+      __syncthreads();
+      unsigned long long cb = s_base[1] + ec;
+      for (int k = tid; k < (int)T; k += kThreads) {
+        int j = 0;
+#pragma unroll
+        for (int st = kThreads / 2; st >= 1; st >>= 1)
+          if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
+        const int v = (int)((t0 + j) * 32 + nth_set_bit(s_nb[j], k - s_wpre[j]));
+        if (v >= p.d) continue;
+        const int64_t nc = (p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk;
+        for (int64_t c = 0; c < nc; ++c) CL[cb++] = make_int2(v, (int)c);
+      }
     }
     __syncthreads();
-    unsigned long long qb = s_base[0] + eq, cb = s_base[1] + ec;
-    __syncthreads();
-    unsigned x = nn;
-    while (x) {
-      const int i = __ffs(x) - 1;
-      x &= x - 1;
-      Q[qb++] = (int)(v0 + i);
+  }
+}
+
+// V |= Ncur and Nclr = 0, 4 words per thread.
+__device__ void merge_bitmaps(const BfsParams& p, const uint32_t* __restrict__ Ncur, uint32_t* __restrict__ Nclr) {
+  const int64_t W4 = (p.words + 3) / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < W4; q += stride) {
+    const uint4 nb4 = __ldcg(reinterpret_cast<const uint4*>(Ncur) + q);
+    if (nb4.x | nb4.y | nb4.z | nb4.w) {
+      uint4 v4 = reinterpret_cast<uint4*>(p.V)[q];
+      v4.x |= nb4.x;
+      v4.y |= nb4.y;
+      v4.z |= nb4.z;
+      v4.w |= nb4.w;
+      reinterpret_cast<uint4*>(p.V)[q] = v4;
     }
-    x = nb & dmask;
-    while (x) {
-      const int i = __ffs(x) - 1;
-      x &= x - 1;
-      const int v = (int)(v0 + i);
-      const int64_t nc = (p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk;
-      for (int64_t k = 0; k < nc; ++k) CL[cb++] = make_int2(v, (int)k);
-    }
+    reinterpret_cast<uint4*>(Nclr)[q] = make_uint4(0, 0, 0, 0);
   }
 }
 
@@ -629,13 +700,34 @@ __device__ void run_body(const BfsParams& p) {
   const bool src_in = src_i < p.n_ni;
   const int64_t sw = src_in ? (src_i >> 5) : -1;
   const unsigned sbit = 1u << (src_i & 31);
-  for (int64_t w = gtid; w < p.words; w += gthreads) {
-    p.V[w] = (w == sw) ? sbit : 0u;
-    p.N0[w] = 0u;
-    p.N1[w] = 0u;
+  const int64_t W4 = (p.words + 3) / 4;
+  for (int64_t q = gtid; q < W4; q += gthreads) {
+    uint4 v4 = make_uint4(0, 0, 0, 0);
+    if (q == (sw >> 2)) {
+      const int t = (int)(sw & 3);
+      v4.x = t == 0 ? sbit : 0u;
+      v4.y = t == 1 ? sbit : 0u;
+      v4.z = t == 2 ? sbit : 0u;
+      v4.w = t == 3 ? sbit : 0u;
+    }
+    reinterpret_cast<uint4*>(p.V)[q] = v4;
+    reinterpret_cast<uint4*>(p.N0)[q] = make_uint4(0, 0, 0, 0);
+    reinterpret_cast<uint4*>(p.N1)[q] = make_uint4(0, 0, 0, 0);
   }
-  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN)
-    for (int64_t v = gtid; v < p.n_ni; v += gthreads) p.parent_i[v] = (v == src_i) ? p.src_c : INT_MAX;
+  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
+    const int64_t P4 = ((int64_t)p.n_ni + 3) / 4;
+    for (int64_t q = gtid; q < P4; q += gthreads) {
+      int4 x = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
+      if (q == ((int64_t)src_i >> 2) && src_in) {
+        const int t = src_i & 3;
+        if (t == 0) x.x = p.src_c;
+        if (t == 1) x.y = p.src_c;
+        if (t == 2) x.z = p.src_c;
+        if (t == 3) x.w = p.src_c;
+      }
+      reinterpret_cast<int4*>(p.parent_i)[q] = x;
+    }
+  }
   unsigned long long src_deg = 0;
   if (src_in) src_deg = (unsigned long long)(p.off[src_i + 1] - p.off[src_i]);
   if (leader) {
@@ -670,6 +762,7 @@ __device__ void run_body(const BfsParams& p) {
   if (!grid_sync(p)) return;
 
   const unsigned long long t_start = gtimer();
+  if (leader) p.hdr->t_init = t_start;
   int L = 0;
   while (!s_done) {
     // Bounds against a run that does not end: at most n_ni+1 levels, and the
@@ -677,6 +770,7 @@ __device__ void run_body(const BfsParams& p) {
     if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
       set_failed(p, BFS_ERR_TIMEOUT);
     const int dir = s_dir;
+    const long long s_unv_level = s_unv;
     LevelSlot* sc = p.slot + (L & (kSlots - 1));
     LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
     uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
@@ -691,7 +785,7 @@ __device__ void run_body(const BfsParams& p) {
     if (dir == 0) {
       expand_td(p, L);
     } else {
-      expand_bu(p, L, acc);
+      expand_bu(p, L, s_unv_level, acc);
       flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
     }
     if (!grid_sync(p)) return;
@@ -707,11 +801,7 @@ __device__ void run_body(const BfsParams& p) {
         flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
       }
     } else {
-      for (int64_t w = gtid; w < p.words; w += gthreads) {
-        const unsigned nb = __ldcg(Ncur + w);
-        if (nb) p.V[w] |= nb;
-        Noth[w] = 0u;
-      }
+      merge_bitmaps(p, Ncur, Noth);
     }
     if (leader) p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
     if (!grid_sync(p)) return;
@@ -749,18 +839,36 @@ __device__ void run_body(const BfsParams& p) {
     ++L;
   }
 
-  // ---- results in caller ids ----
-  for (int64_t c = gtid; c < p.n; c += gthreads) {
-    const int v = p.internal_of[c];
-    const bool r = v < p.n_ni && ((p.V[v >> 5] >> (v & 31)) & 1u);
-    int dv = r ? p.depth_i[v] : -1;
-    int pv = r ? p.parent_i[v] : -1;
-    if (c == p.src_c) {
-      dv = 0;
-      pv = p.src_c;
+  // ---- results in caller ids: 4 consecutive caller ids per thread ----
+  if (leader) p.hdr->t_loop = gtimer();
+  const int64_t C4 = ((int64_t)p.n + 3) / 4;
+  for (int64_t q = gtid; q < C4; q += gthreads) {
+    const int4 iv = reinterpret_cast<const int4*>(p.internal_of)[q];
+    const int vs[4] = {iv.x, iv.y, iv.z, iv.w};
+    int dv[4], pv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int v = vs[t];
+      const bool r = v >= 0 && v < p.n_ni && ((p.V[v >> 5] >> (v & 31)) & 1u);
+      dv[t] = r ? p.depth_i[v] : -1;
+      pv[t] = r ? p.parent_i[v] : -1;
+      if (q * 4 + t == p.src_c) {
+        dv[t] = 0;
+        pv[t] = p.src_c;
+      }
     }
-    p.out_depth[c] = dv;
-    p.out_parent[c] = pv;
+    const int64_t c = q * 4;
+    if (p.out_vec4 && c + 3 < p.n) {
+      reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
+      reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c + t < p.n) {
+          p.out_depth[c + t] = dv[t];
+          p.out_parent[c + t] = pv[t];
+        }
+    }
   }
   if (leader) {
     p.hdr->levels = src_in ? L : 1;
@@ -826,6 +934,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.timeout_ns = (unsigned long long)g->opt.barrier_timeout_ms * 1000000ull;
   p.test_skip_barrier = g->opt.test_skip_barrier;
   p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
+  p.out_vec4 = ((((uintptr_t)out_depth) | ((uintptr_t)out_parent)) & 15) == 0;
   p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
   void* args[] = {&p};

@@ -270,7 +270,8 @@ int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, co
 
   // 5. renumbering, offsets, columns
   int64_t dev_bytes = 0;
-  BFS_CUDA(cudaMalloc(&g->internal_of, (size_t)n * 4), "alloc internal_of");
+  BFS_CUDA(cudaMalloc(&g->internal_of, ((size_t)n + 4) * 4), "alloc internal_of");
+  BFS_CUDA(cudaMemsetAsync(g->internal_of, 0x7F, ((size_t)n + 4) * 4, s), "memset");
   BFS_CUDA(cudaMalloc(&g->caller_of, (size_t)n * 4), "alloc caller_of");
   BFS_CUDA(cudaMalloc(&g->off, ((size_t)g->n_ni + 1) * 8), "alloc row offsets");
   dev_bytes += (int64_t)n * 8 + ((int64_t)g->n_ni + 1) * 8;
