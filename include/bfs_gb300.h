@@ -64,12 +64,14 @@ typedef struct bfs_options {
   double factor0;           /* BFS_SCHED_PAPER: forward->backward when FV > factor0 * BV (default 0.5) */
   double factor1;           /* BFS_SCHED_PAPER: backward->forward when FV < factor1 * BV (default 1e-7) */
   int32_t td_parent;        /* BFS_TD_PARENT_* (default ATOMICMIN) */
-  int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM (0 = as many as fit) */
+  int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM: 0 or 2 = the 64-register build,
+                               3 = the 40-register build (3 CTAs of 512 threads per SM) */
   int32_t barrier_timeout_ms; /* bound of every device-side grid-barrier wait (default 2000) */
   int32_t test_skip_barrier;  /* testing only: CTA 0 leaves before the first grid barrier, so the
                                  other CTAs' bounded wait expires and the run reports BFS_ERR_TIMEOUT */
   int32_t run_timeout_ms;     /* bound of one run's device time (default 60000): BFS_ERR_TIMEOUT */
-  int32_t reserved[5];
+  int32_t tuning;             /* bit 0: forward visits read the discovered word before an atomicOr */
+  int32_t reserved[4];
 } bfs_options;
 
 /* Fills *opt with the defaults: th 64, host edges, Beamer alpha 15 / beta 18,

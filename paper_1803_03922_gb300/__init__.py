@@ -46,7 +46,8 @@ class bfs_options(ctypes.Structure):
     _fields_ = [("th", c_i64), ("edges_on_device", c_i32), ("schedule", c_i32), ("schedule_mask", c_u64),
                 ("alpha", c_i32), ("beta", c_i32), ("factor0", c_dbl), ("factor1", c_dbl),
                 ("td_parent", c_i32), ("blocks_per_sm", c_i32), ("barrier_timeout_ms", c_i32),
-                ("test_skip_barrier", c_i32), ("run_timeout_ms", c_i32), ("reserved", c_i32 * 5)]
+                ("test_skip_barrier", c_i32), ("run_timeout_ms", c_i32), ("tuning", c_i32),
+                ("reserved", c_i32 * 4)]
 
 
 class bfs_graph_info(ctypes.Structure):

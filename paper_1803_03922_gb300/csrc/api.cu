@@ -60,7 +60,8 @@ int check_options(const bfs_options& o) {
   if (o.alpha <= 0 || o.beta <= 0) return fail(BFS_ERR_INVALID, "alpha and beta must be > 0");
   if (o.td_parent != BFS_TD_PARENT_PULL && o.td_parent != BFS_TD_PARENT_ATOMICMIN)
     return fail(BFS_ERR_INVALID, "unknown td_parent");
-  if (o.blocks_per_sm < 0) return fail(BFS_ERR_INVALID, "blocks_per_sm must be >= 0");
+  if (o.blocks_per_sm < 0 || o.blocks_per_sm == 1 || o.blocks_per_sm > 3)
+    return fail(BFS_ERR_INVALID, "blocks_per_sm must be 0, 2 or 3");
   if (o.barrier_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "barrier_timeout_ms must be > 0");
   if (o.run_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "run_timeout_ms must be > 0");
   if (!(o.factor0 >= 0) || !(o.factor1 >= 0)) return fail(BFS_ERR_INVALID, "factors must be >= 0");
@@ -92,7 +93,7 @@ int alloc_run_state(bfs_graph* g) {
 }
 
 void free_all(bfs_graph* g) {
-  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->V, g->N0, g->N1, g->depth_i,
+  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->V, g->N0, g->N1, g->depth_i,
                   g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->slot, g->log, g->hdr, g->out_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -14,6 +14,7 @@ constexpr int kThreads = 512;         // level-loop CTA size (16 warps)
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
+constexpr int kHead = 4;              // row entries kept in the per-vertex head record
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Per-level counters; a ring of kSlots indexed by level.
@@ -54,6 +55,8 @@ struct BfsParams {
   const int32_t* col;        // [nnz + kColPad]
   const int32_t* caller_of;  // [n]
   const int32_t* internal_of;// [n]
+  const int4* head;          // [2 n_ni]: first kHead neighbours (internal ids, -1 pad), then their caller ids
+  const int32_t* deg;        // [n_ni] degree
   uint32_t* V;               // visited bitmap, [words]
   uint32_t* N0;              // discovered-this-level bitmaps, [words] each
   uint32_t* N1;
@@ -82,6 +85,7 @@ struct BfsParams {
   int32_t test_skip_barrier; // testing only: CTA 0 skips the first barrier
   unsigned long long run_timeout_ns;
   int32_t out_vec4;          // out_depth/out_parent are 16-byte aligned
+  int32_t tuning;            // bfs_options.tuning
 };
 
 }  // namespace bfsgb
@@ -100,6 +104,8 @@ struct bfs_graph {
   int32_t* col = nullptr;
   int32_t* caller_of = nullptr;
   int32_t* internal_of = nullptr;
+  int4* head = nullptr;
+  int32_t* deg = nullptr;
   // run state
   uint32_t* V = nullptr;
   uint32_t* N0 = nullptr;
@@ -115,6 +121,7 @@ struct bfs_graph {
   bfsgb::RunHeader* hdr = nullptr;
   int32_t* out_scratch = nullptr;  // [2n], for runs with host output buffers
   int grid_blocks = 0;
+  int variant = 2;                 // CTAs per SM of the level-loop build in use
   unsigned int epoch = 0;          // runs launched
 };
 

@@ -211,38 +211,20 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
   return -1;
 }
 
-// Pull scan, one vertex per lane: lanes with `act` scan their row [beg,end) in
-// order and stop at the first neighbour passing the probe.
-//  A: each lane reads the first kWin entries of its own row;
+// Phases B and C of a pull scan: lanes with `more` have scanned the first
+// kHead entries of their row [beg,end) without a hit.
 //  B: rows with at most kShort entries left go to 8-lane groups, four rows at a
 //     time, one 32-byte sector per group and step;
 //  C: longer rows are finished by the whole warp, one row at a time, 128 entries
 //     per step.
-// Returns the neighbour's internal id or -1; kv = entries examined (first-hit
-// position + 1, or the degree).
+// On a hit, hit/k are set (k = first-hit position + 1); otherwise k = end - beg.
 template <bool kFix>
-__device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end,
-                          const uint32_t* __restrict__ Ncur, int64_t& kv) {
-  constexpr int kWin = 4;
+__device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t end, const uint32_t* __restrict__ Ncur,
+                          int& hit, int64_t& k) {
   constexpr int64_t kShort = 64;
   const int lane = lane_id();
-  int hit = -1;
-  int64_t k = 0;
-  if (act) {
-    const int64_t lim = min(end, beg + kWin);
-    int c[kWin];
-#pragma unroll
-    for (int t = 0; t < kWin; ++t) c[t] = (beg + t < lim) ? p.col[beg + t] : -1;
-#pragma unroll
-    for (int t = 0; t < kWin; ++t)
-      if (hit < 0 && c[t] >= 0 && probe<kFix>(p, c[t], Ncur)) {
-        hit = c[t];
-        k = t + 1;
-      }
-    if (hit < 0) k = lim - beg;
-  }
-  const bool more = act && hit < 0 && beg + kWin < end;
-  const bool longrow = more && (end - beg - kWin) > kShort;
+  if (more) k = end - beg;
+  const bool longrow = more && (end - beg - kHead) > kShort;
   unsigned rem = __ballot_sync(kFull, more && !longrow);
   const int g = lane >> 3, sub = lane & 7;
   while (rem) {
@@ -255,7 +237,7 @@ __device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end
     bool gdone = g >= take;
     int ghit = -1;
     int64_t gk = 0;
-    int64_t pos = rbeg + kWin;
+    int64_t pos = rbeg + kHead;
     while (__any_sync(kFull, !gdone)) {
       const int64_t j = pos + sub;
       const int c = (!gdone && j < rend) ? p.col[j] : -1;
@@ -296,13 +278,88 @@ __device__ int pull_lanes(const BfsParams& p, bool act, int64_t beg, int64_t end
     const int64_t rbeg = __shfl_sync(kFull, beg, owner);
     const int64_t rend = __shfl_sync(kFull, end, owner);
     int64_t k2;
-    const int h2 = warp_scan<kFix>(p, rbeg, rbeg + kWin, rend, Ncur, k2);
+    const int h2 = warp_scan<kFix>(p, rbeg, rbeg + kHead, rend, Ncur, k2);
     if (lane == owner) {
       hit = h2;
       k = k2;
     }
   }
+}
+
+// Phase A of a pull scan, one vertex per lane: loads the head record of v (its
+// first kHead neighbours and their caller ids, one coalesced sector) and its
+// degree.  Split from the probes so a caller can put several vertices' loads in
+// flight before the first probe.
+struct HeadRec {
+  int4 nb, cid;
+  int deg;
+};
+
+__device__ __forceinline__ HeadRec head_load(const BfsParams& p, bool act, int v) {
+  HeadRec h;
+  h.nb = make_int4(-1, -1, -1, -1);
+  h.cid = h.nb;
+  h.deg = 0;
+  if (act) {
+    h.nb = __ldg(p.head + 2 * (int64_t)v);
+    h.cid = __ldg(p.head + 2 * (int64_t)v + 1);
+    h.deg = __ldg(p.deg + v);
+  }
+  return h;
+}
+
+// Probes the head entries of a loaded record: first hit (internal id, caller
+// id) and k = its position + 1, or k = min(degree, kHead) and hit = -1.
+template <bool kFix>
+__device__ __forceinline__ void head_probe(const BfsParams& p, const HeadRec& h, const uint32_t* __restrict__ Ncur,
+                                           int& hit, int& cid, int64_t& k) {
+  const int nb[kHead] = {h.nb.x, h.nb.y, h.nb.z, h.nb.w};
+  const int cs[kHead] = {h.cid.x, h.cid.y, h.cid.z, h.cid.w};
+  bool hh[kHead];
+#pragma unroll
+  for (int t = 0; t < kHead; ++t) hh[t] = nb[t] >= 0 && probe<kFix>(p, nb[t], Ncur);
+  hit = -1;
+  cid = -1;
+  k = h.deg < kHead ? h.deg : kHead;
+#pragma unroll
+  for (int t = kHead - 1; t >= 0; --t)
+    if (hh[t]) {
+      hit = nb[t];
+      cid = cs[t];
+      k = t + 1;
+    }
+}
+
+// Phases B/C for the lanes whose row continues past the head entries without a
+// hit: loads the row offset and finishes the scan (warp-collective).
+template <bool kFix>
+__device__ __forceinline__ void pull_tail(const BfsParams& p, bool act, int v, int deg,
+                                          const uint32_t* __restrict__ Ncur, int& hit, int& cid, int64_t& k) {
+  const bool more = act && hit < 0 && deg > kHead;
+  int64_t beg = 0, end = 0;
+  if (more) {
+    beg = p.off[v];
+    end = beg + deg;
+  }
+  pull_rest<kFix>(p, more, beg, end, Ncur, hit, k);
+  if (more && hit >= 0) cid = p.caller_of[hit];
+}
+
+// Pull scan, one vertex per lane: lanes with `act` scan the row of v in order
+// and stop at the first neighbour passing the probe.  Returns the neighbour's
+// internal id or -1, its caller id in hit_cid, kv = entries examined (first-hit
+// position + 1, or the degree), and the degree.
+template <bool kFix>
+__device__ int pull_head(const BfsParams& p, bool act, int v, const uint32_t* __restrict__ Ncur, int64_t& kv,
+                         int& hit_cid, int& degree) {
+  const HeadRec h = head_load(p, act, v);
+  int hit = -1, cid = -1;
+  int64_t k = 0;
+  if (act) head_probe<kFix>(p, h, Ncur, hit, cid, k);
+  pull_tail<kFix>(p, act, v, h.deg, Ncur, hit, cid, k);
   kv = k;
+  hit_cid = cid;
+  degree = h.deg;
   return hit;
 }
 
@@ -317,7 +374,7 @@ __device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, 
   const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
   if (p.V[w] & bit) return;
   if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
-  atomicOr(N + w, bit);
+  if (!(p.tuning & 1) || !(__ldcg(N + w) & bit)) atomicOr(N + w, bit);
 }
 
 // Four row entries of one lane: the four visited-bit probes are issued before
@@ -330,7 +387,9 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const int (&v)[4], 
   for (int t = 0; t < 4; ++t) {
     if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
     if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], pcaller);
-    atomicOr(N + ((unsigned)v[t] >> 5), 1u << (v[t] & 31));
+    uint32_t* nw = N + ((unsigned)v[t] >> 5);
+    const unsigned bit = 1u << (v[t] & 31);
+    if (!(p.tuning & 1) || !(__ldcg(nw) & bit)) atomicOr(nw, bit);
   }
 }
 
@@ -346,7 +405,7 @@ __device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int
   int pc = 0;
   if (u >= 0) {
     beg = p.off[u];
-    deg = p.off[u + 1] - beg;
+    deg = p.deg[u];
     if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) pc = p.caller_of[u];
   }
   const int64_t incl = warp_incl_scan(deg);
@@ -375,12 +434,19 @@ __device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) 
   const int64_t beg = rb + (int64_t)ck.y * kChunk;
   const int64_t end = min(beg + kChunk, re);
   const int pc = (p.td_parent == BFS_TD_PARENT_ATOMICMIN) ? p.caller_of[u] : 0;
-  for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 128) {
-    const int64_t j = j0 + lane * 4;
-    if (j < end) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
-      const int v[4] = {j >= beg ? c4.x : -1, (j + 1 >= beg && j + 1 < end) ? c4.y : -1,
-                        (j + 2 >= beg && j + 2 < end) ? c4.z : -1, (j + 3 >= beg && j + 3 < end) ? c4.w : -1};
+  // two 128-bit column loads per lane per step (256 entries per warp)
+  for (int64_t j0 = beg & ~(int64_t)3; j0 < end; j0 += 256) {
+    const int64_t ja = j0 + lane * 4, jb = ja + 128;
+    int4 ca = make_int4(-1, -1, -1, -1), cb = ca;
+    if (ja < end) ca = __ldg(reinterpret_cast<const int4*>(p.col + ja));
+    if (jb < end) cb = __ldg(reinterpret_cast<const int4*>(p.col + jb));
+    if (ja < end) {
+      const int v[4] = {ja >= beg ? ca.x : -1, (ja + 1 >= beg && ja + 1 < end) ? ca.y : -1,
+                        (ja + 2 >= beg && ja + 2 < end) ? ca.z : -1, (ja + 3 >= beg && ja + 3 < end) ? ca.w : -1};
+      td_edge4(p, v, pc, N);
+    }
+    if (jb < end) {
+      const int v[4] = {cb.x, jb + 1 < end ? cb.y : -1, jb + 2 < end ? cb.z : -1, jb + 3 < end ? cb.w : -1};
       td_edge4(p, v, pc, N);
     }
   }
@@ -426,11 +492,16 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // Items of iw bitmap words (iw = 4..32, larger when few vertices are left);
 // warp w takes items w, w + warps, ...  The unvisited vertices of an item are
 // gathered 32 at a time (lane i takes the i-th one), so a sparse item costs one
-// batch, not one pass per word.  A vertex that finds its parent gets depth,
-// parent and its bit in N.
+// batch, not one pass per word.  A vertex that finds its parent gets depth and
+// parent; its bit is collected in the warp's shared-memory copy of the item's
+// words, which the warp owns, and each word is written to N once.
 __device__ void expand_bu(const BfsParams& p, int L, long long unvisited, Acc& acc) {
+  __shared__ unsigned s_found[kWarpsPerBlock][32];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
+  unsigned* found = s_found[threadIdx.x >> 5];
+  found[lane] = 0u;
+  __syncwarp();
   const int64_t W = p.words;
   // about 64 unvisited vertices per item: iw ~ 2 n_ni / unvisited words
   int iw = 4;
@@ -455,39 +526,68 @@ __device__ void expand_bu(const BfsParams& p, int L, long long unvisited, Acc& a
       if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(kFull, incl, 31);
-    for (int b = 0; b < total; b += 32) {
-      const int k = b + lane;
-      const bool act = k < total;
-      int j = 0;  // word of the k-th unvisited vertex: first lane whose prefix exceeds k
+    const int excl = incl - cnt;
+    // the k-th unvisited vertex of the item: word = first lane whose prefix exceeds k
+    auto locate = [&](int k, int64_t& word, int& bit) {
+      int j = 0;
 #pragma unroll
       for (int s = 16; s >= 1; s >>= 1) {
         const int t = __shfl_sync(kFull, incl, j + s - 1);
         if (t <= k) j += s;
       }
       const unsigned m = __shfl_sync(kFull, unv, j);
-      const int ex = __shfl_sync(kFull, incl - cnt, j);
-      const int bit = act ? nth_set_bit(m, k - ex) : 0;
-      const int64_t word = it * iw + j;
-      const int v = (int)(word * 32 + bit);
-      int64_t beg = 0, end = 0;
-      if (act) {
-        beg = p.off[v];
-        end = p.off[v + 1];
-      }
-      int64_t kv = 0;
-      const int hit = pull_lanes<false>(p, act, beg, end, nullptr, kv);
-      if (act) {
+      const int ex = __shfl_sync(kFull, excl, j);
+      bit = k < total ? nth_set_bit(m, k - ex) : 0;
+      word = it * iw + j;
+    };
+    // two batches of 32 vertices per step: both head records are loaded, and
+    // all eight head probes issued, before either batch waits on a result
+    for (int b = 0; b < total; b += 64) {
+      int64_t wA, wB;
+      int bA, bB;
+      locate(b + lane, wA, bA);
+      locate(b + 32 + lane, wB, bB);
+      const bool aA = b + lane < total, aB = b + 32 + lane < total;
+      const int vA = (int)(wA * 32 + bA), vB = (int)(wB * 32 + bB);
+      const HeadRec hA = head_load(p, aA, vA);
+      const HeadRec hB = head_load(p, aB, vB);
+      int hitA = -1, cidA = -1, hitB = -1, cidB = -1;
+      int64_t kA = 0, kB = 0;
+      if (aA) head_probe<false>(p, hA, nullptr, hitA, cidA, kA);
+      if (aB) head_probe<false>(p, hB, nullptr, hitB, cidB, kB);
+      pull_tail<false>(p, aA, vA, hA.deg, nullptr, hitA, cidA, kA);
+      pull_tail<false>(p, aB, vB, hB.deg, nullptr, hitB, cidB, kB);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const bool act = q ? aB : aA;
+        const int hit = q ? hitB : hitA;
+        const int v = q ? vB : vA;
+        const int64_t word = q ? wB : wA;
+        // lanes of one batch that share a word are adjacent: OR their bits
+        const unsigned fbit = (act && hit >= 0) ? (1u << (q ? bB : bA)) : 0u;
+        const unsigned grp = __match_any_sync(kFull, (unsigned)(word - it * iw));
+        const unsigned orb = __reduce_or_sync(grp, fbit);
+        if (orb && lane == __ffs(grp) - 1) found[word - it * iw] |= orb;
+        if (!act) continue;
         acc.scanned += 1;
-        acc.edges += (unsigned long long)kv;
+        acc.edges += (unsigned long long)(q ? kB : kA);
         if (hit >= 0) {
-          p.parent_i[v] = p.caller_of[hit];
+          p.parent_i[v] = q ? cidB : cidA;
           p.depth_i[v] = L + 1;
-          atomicOr(N + word, 1u << bit);
           acc.nf += 1;
-          acc.mf += (unsigned long long)(end - beg);
+          acc.mf += (unsigned long long)(q ? hB.deg : hA.deg);
         }
       }
+      __syncwarp();
     }
+    if (lane < iw) {
+      const unsigned f = found[lane];
+      if (f) {
+        N[it * iw + lane] = f;
+        found[lane] = 0u;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -534,27 +634,47 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
     const unsigned long long qbase = s_base[0];
     const bool has_del = t0 * 32 < p.d;
     unsigned long long nch_local = 0;
-    for (int k = tid; k < (int)T; k += kThreads) {
-      int j = 0;
+    // four new vertices per thread and step, so their degree loads overlap
+    for (int k0 = tid; k0 < (int)T; k0 += 4 * kThreads) {
+      int vv[4], jj[4], bb[4];
 #pragma unroll
-      for (int st = kThreads / 2; st >= 1; st >>= 1)
-        if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
-      const unsigned m = s_nb[j];
-      const int bit = nth_set_bit(m, k - s_wpre[j]);
-      const int v = (int)((t0 + j) * 32 + bit);
-      const int64_t deg = p.off[v + 1] - p.off[v];
-      if (count) {
-        p.depth_i[v] = depth;
-        acc.nf += 1;
-        acc.mf += (unsigned long long)deg;
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * kThreads;
+        int j = 0;
+        if (k < (int)T) {
+#pragma unroll
+          for (int st = kThreads / 2; st >= 1; st >>= 1)
+            if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
+          bb[u] = nth_set_bit(s_nb[j], k - s_wpre[j]);
+          vv[u] = (int)((t0 + j) * 32 + bb[u]);
+        } else {
+          bb[u] = 0;
+          vv[u] = -1;
+        }
+        jj[u] = j;
       }
-      if (v >= p.d) {
-        const int64_t jv0 = (t0 + j) * 32;
-        unsigned jd = 0;
-        if (jv0 < p.d) jd = (p.d - jv0 >= 32) ? kFull : ((1u << (p.d - jv0)) - 1u);
-        Q[qbase + s_npre[j] + __popc(m & ~jd & ((1u << bit) - 1u))] = v;
-      } else {
-        nch_local += (unsigned long long)((deg + kChunk - 1) / kChunk);
+      int dg[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) dg[u] = vv[u] >= 0 ? p.deg[vv[u]] : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int v = vv[u];
+        if (v < 0) continue;
+        const int64_t deg = dg[u];
+        if (count) {
+          p.depth_i[v] = depth;
+          acc.nf += 1;
+          acc.mf += (unsigned long long)deg;
+        }
+        if (v >= p.d) {
+          const int j = jj[u];
+          const int64_t jv0 = (t0 + j) * 32;
+          unsigned jd = 0;
+          if (jv0 < p.d) jd = (p.d - jv0 >= 32) ? kFull : ((1u << (p.d - jv0)) - 1u);
+          Q[qbase + s_npre[j] + __popc(s_nb[j] & ~jd & ((1u << bb[u]) - 1u))] = v;
+        } else {
+          nch_local += (unsigned long long)((deg + kChunk - 1) / kChunk);
+        }
       }
     }
     if (has_del) {
@@ -570,7 +690,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
           if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
         const int v = (int)((t0 + j) * 32 + nth_set_bit(s_nb[j], k - s_wpre[j]));
         if (v >= p.d) continue;
-        const int64_t nc = (p.off[v + 1] - p.off[v] + kChunk - 1) / kChunk;
+        const int64_t nc = ((int64_t)p.deg[v] + kChunk - 1) / kChunk;
         for (int64_t c = 0; c < nc; ++c) CL[cb++] = make_int2(v, (int)c);
       }
     }
@@ -612,16 +732,12 @@ __device__ void pull_parents(const BfsParams& p, int L, Acc& acc) {
     const int64_t i = b * 32 + lane;
     const bool act = i < qn;
     const int v = act ? Qn[i] : 0;
-    int64_t beg = 0, end = 0;
-    if (act) {
-      beg = p.off[v];
-      end = p.off[v + 1];
-    }
     int64_t kv = 0;
-    const int hit = pull_lanes<true>(p, act, beg, end, Ncur, kv);
+    int cid = -1, deg = 0;
+    const int hit = pull_head<true>(p, act, v, Ncur, kv, cid, deg);
     if (act) {
       acc.fix += (unsigned long long)kv;
-      if (hit >= 0) p.parent_i[v] = p.caller_of[hit];
+      if (hit >= 0) p.parent_i[v] = cid;
     }
   }
   for (int64_t e = gwarp; e < nch; e += nwarps) {
@@ -681,7 +797,10 @@ __device__ void block_exit(const BfsParams& p) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) bfs_level_loop(BfsParams p) {
+// Two builds of the same kernel: 2 CTAs of 512 threads per SM (64 registers) or
+// 3 (40 registers, some spilled to local memory).
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) bfs_level_loop(BfsParams p) {
   run_body(p);
   block_exit(p);
 }
@@ -889,11 +1008,13 @@ int configure_run(bfs_graph* g) {
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   if (!coop) return fail(BFS_ERR_CUDA, "device does not support cooperative launch");
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop, kThreads, 0);
+  const int variant = g->opt.blocks_per_sm == 3 ? 3 : 2;
+  e = variant == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<3>, kThreads, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<2>, kThreads, 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level-loop kernel does not fit on an SM");
-  int want = g->opt.blocks_per_sm > 0 ? g->opt.blocks_per_sm : per_sm;
-  if (want > per_sm) want = per_sm;
+  const int want = per_sm < variant ? per_sm : variant;
+  g->variant = variant;
   g->grid_blocks = sms * want;
   return BFS_OK;
 }
@@ -904,6 +1025,8 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.col = g->col;
   p.caller_of = g->caller_of;
   p.internal_of = g->internal_of;
+  p.head = g->head;
+  p.deg = g->deg;
   p.V = g->V;
   p.N0 = g->N0;
   p.N1 = g->N1;
@@ -935,11 +1058,12 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.test_skip_barrier = g->opt.test_skip_barrier;
   p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
   p.out_vec4 = ((((uintptr_t)out_depth) | ((uintptr_t)out_parent)) & 15) == 0;
+  p.tuning = g->opt.tuning;
   p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
   void* args[] = {&p};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)bfs_level_loop, dim3(g->grid_blocks), dim3(kThreads),
-                                              args, 0, s);
+  const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3> : (const void*)bfs_level_loop<2>;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid_blocks), dim3(kThreads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
   return BFS_OK;
 }
