@@ -166,6 +166,27 @@ int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* parent, bfs_s
  * device buffers and no stats do not report it themselves). */
 int bfs_wait(bfs_graph* g, struct CUstream_st* stream);
 
+/* BFS for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this entry point exists for code that runs where cudaMalloc is
+ * not available to it (inside another runtime that owns the device allocator,
+ * or under a fixed allocation budget).  It allocates nothing; all its scratch is
+ * one fixed-size __device__ array of this library (about 6 MiB, held on every
+ * device that loads the library until the process exits).
+ *   row_off[n+1] int64, col[row_off[n]] int32: caller-owned DEVICE memory, a
+ *     symmetric CSR in the caller's ids with every row sorted ascending and no
+ *     self-loops or repeated entries (the graph bfs_build_graph would build).
+ *   n: 1 .. 16,777,216 vertices; larger n returns BFS_ERR_OVERFLOW, nothing runs.
+ *   depth[n], parent[n]: caller-owned DEVICE int32 buffers; same results as
+ *     bfs_run (hop distance, canonical smallest-id parent, -1 unreached).
+ * The first call on a device looks up the scratch array's device address (make
+ * that first call before any stream capture).  Every call shares the scratch and
+ * clears what it needs at its start; calls that overlap on the GPU (for example
+ * on two streams) race and must not be issued.  Synchronizes `stream` and
+ * returns BFS_OK, BFS_ERR_TIMEOUT (a bounded device wait expired), INVALID,
+ * OVERFLOW or CUDA. */
+int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_t n, int32_t source, int32_t* depth,
+                   int32_t* parent, struct CUstream_st* stream);
+
 /* Releases every device and host resource of the graph.  NULL is a no-op. */
 void bfs_free(bfs_graph* g);
 

@@ -95,6 +95,7 @@ def _load():
     lib.bfs_graph_export.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
     lib.bfs_run.argtypes = [c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(bfs_stats), c_vp]
     lib.bfs_wait.argtypes = [c_vp, c_vp]
+    lib.bfs_run_static.argtypes = [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]
     lib.bfs_free.argtypes = [c_vp]
     lib.bfs_free.restype = None
     lib.bfs_last_error.restype = ctypes.c_char_p
@@ -207,6 +208,13 @@ def bfs_run(g, source: int, depth, parent, stats: bfs_stats | None = None, strea
 
 def bfs_wait(g, stream=None):
     _check(_load().bfs_wait(g, _stream(stream)))
+
+
+def bfs_run_static(row_off, col, n: int, source: int, depth, parent, stream=None):
+    """The allocation-free entry point: caller-owned device CSR (int64 offsets,
+    int32 sorted symmetric columns) and device result buffers."""
+    _check(_load().bfs_run_static(_ptr(row_off), _ptr(col), int(n), int(source), _ptr(depth), _ptr(parent),
+                                  _stream(stream)))
 
 
 def bfs_free(g):
