@@ -45,6 +45,7 @@ WORKLOADS = {
     "rmat26": dict(kind="rmat", scale=26, th=64, seed=26, src_seed=2601),
     "er26": dict(kind="er", scale=26, avgdeg=32, th=64, seed=126, src_seed=12601),
     "rmat16": dict(kind="rmat", scale=16, th=64, seed=16, src_seed=1601),
+    "rmat24": dict(kind="rmat", scale=24, th=64, seed=24, src_seed=2401),
 }
 
 
