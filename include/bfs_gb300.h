@@ -134,6 +134,7 @@ typedef struct bfs_level_log {
   int64_t found;          /* |F_{L+1}| */
   int64_t queue_entries;  /* normal-vertex queue entries holding F_L (forward levels) */
   uint64_t t_begin_ns, t_expand_ns, t_end_ns; /* device %globaltimer at the phase edges */
+  uint64_t t_first_done_ns, t_last_done_ns;   /* when the first / last CTA finished the expansion */
 } bfs_level_log;
 
 typedef struct bfs_stats {

@@ -59,7 +59,8 @@ class bfs_graph_info(ctypes.Structure):
 class bfs_level_log(ctypes.Structure):
     _fields_ = [("direction", c_i32), ("converted", c_i32), ("frontier", c_i64), ("frontier_edges", c_i64),
                 ("scanned", c_i64), ("edges_examined", c_i64), ("parent_edges", c_i64), ("found", c_i64),
-                ("queue_entries", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64)]
+                ("queue_entries", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64),
+                ("t_first_done_ns", c_u64), ("t_last_done_ns", c_u64)]
 
 
 class bfs_stats(ctypes.Structure):

@@ -73,6 +73,7 @@ int alloc_run_state(bfs_graph* g) {
   g->words = ((int64_t)g->n_ni + 31) / 32;
   const size_t words = (size_t)g->words + 32;
   int rc;
+  cudaError_t e;
   if ((rc = dmalloc(&g->V, words, &t, "alloc V"))) return rc;
   if ((rc = dmalloc(&g->N0, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->N1, words, &t, "alloc N"))) return rc;
@@ -82,10 +83,14 @@ int alloc_run_state(bfs_graph* g) {
   if ((rc = dmalloc(&g->Q1, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
   if ((rc = dmalloc(&g->CL0, (size_t)g->cl_cap, &t, "alloc chunk list"))) return rc;
   if ((rc = dmalloc(&g->CL1, (size_t)g->cl_cap, &t, "alloc chunk list"))) return rc;
+  if ((rc = dmalloc(&g->longq, (size_t)g->long_cap, &t, "alloc long-row list"))) return rc;
   if ((rc = dmalloc(&g->slot, (size_t)kSlots, &t, "alloc counters"))) return rc;
   if ((rc = dmalloc(&g->log, (size_t)BFS_LOG_LEVELS, &t, "alloc log"))) return rc;
   if ((rc = dmalloc(&g->hdr, 1, &t, "alloc header"))) return rc;
-  cudaError_t e = cudaMemset(g->hdr, 0, sizeof(RunHeader));
+  if ((rc = dmalloc(&g->arrive, (size_t)kMaxBlocks * 4, &t, "alloc barrier words"))) return rc;
+  e = cudaMemset(g->arrive, 0, sizeof(unsigned long long) * kMaxBlocks * 4);
+  if (e != cudaSuccess) return cuda_fail(e, "memset barrier words");
+  e = cudaMemset(g->hdr, 0, sizeof(RunHeader));
   if (e != cudaSuccess) return cuda_fail(e, "memset header");
   e = cudaMemset(g->slot, 0, sizeof(LevelSlot) * kSlots);
   if (e != cudaSuccess) return cuda_fail(e, "memset counters");
@@ -94,7 +99,7 @@ int alloc_run_state(bfs_graph* g) {
 
 void free_all(bfs_graph* g) {
   void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->V, g->N0, g->N1, g->depth_i,
-                  g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->slot, g->log, g->hdr, g->out_scratch};
+                  g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -272,6 +277,8 @@ static int fill_stats(bfs_graph* g, bfs_stats* st, const RunHeader& h) {
       o.t_begin_ns = lg[L].t_begin;
       o.t_expand_ns = lg[L].t_expand;
       o.t_end_ns = lg[L].t_end;
+      o.t_first_done_ns = lg[L].t_first;
+      o.t_last_done_ns = lg[L].t_last;
       st->edges_examined += o.edges_examined;
     }
   }

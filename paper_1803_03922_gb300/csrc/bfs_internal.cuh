@@ -15,7 +15,9 @@ constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
 constexpr int kHead = 4;              // row entries kept in the per-vertex head record
+constexpr int64_t kShort = 64;        // rows with more entries left after the head go to the long-row path
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kMaxBlocks = 2048;      // upper bound of the level-loop grid (arrival words)
 
 // Per-level counters; a ring of kSlots indexed by level.
 struct __align__(64) LevelSlot {
@@ -27,20 +29,24 @@ struct __align__(64) LevelSlot {
   unsigned long long edges;     // backward: sum of k_v
   unsigned long long scanned;   // backward: unvisited vertices scanned
   unsigned long long fix_edges; // forward: row entries read to pick parents
+  unsigned long long t_first;   // %globaltimer when the first / last CTA finished the expansion
+  unsigned long long t_last;
+  unsigned long long work2;     // hand-out counter of the deferred long rows
+  unsigned long long nlong;     // deferred long rows (backward)
+  unsigned long long pad[4];
 };
 constexpr int kSlots = 4;
 
 struct LevelLogDev {
   int32_t dir, converted;
   unsigned long long n_f, m_f, scanned, edges, fix_edges, found, qn;
-  unsigned long long t_begin, t_expand, t_end;
+  unsigned long long t_begin, t_expand, t_end, t_first, t_last;
 };
 
 struct RunHeader {
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned long long release;  // last released grid barrier: (epoch << 36) | (seq << 8) | decision bits
   unsigned int err;    // (epoch << 4) | -BFS_ERR_*, written by the device on failure
-  unsigned int exited; // CTAs that left the kernel (the last one resets the barrier)
+  unsigned int exited; // unused
   int levels;          // max depth + 1
   int levels_run;      // levels executed by the loop (0 for an isolated source)
   unsigned long long t0, t1;
@@ -62,6 +68,7 @@ struct BfsParams {
   uint32_t* N1;
   int32_t* depth_i;          // [n_ni]
   int32_t* parent_i;         // [n_ni], caller ids
+  int32_t* longq;            // vertices whose backward scan is deferred to the end of the level, [long_cap]
   int32_t* Q0;               // normal-vertex frontier queues, [n_ni] each
   int32_t* Q1;
   int2* CL0;                 // delegate chunk lists (vertex, chunk), [cl_cap] each
@@ -69,6 +76,7 @@ struct BfsParams {
   LevelSlot* slot;           // [kSlots]
   LevelLogDev* log;          // [BFS_LOG_LEVELS]
   RunHeader* hdr;
+  unsigned long long* arrive;// grid-barrier arrival words, one per CTA, 32 bytes apart
   int32_t* out_depth;        // [n] caller-indexed
   int32_t* out_parent;       // [n]
   int64_t nnz;
@@ -116,9 +124,12 @@ struct bfs_graph {
   int32_t* Q1 = nullptr;
   int2* CL0 = nullptr;
   int2* CL1 = nullptr;
+  int32_t* longq = nullptr;
+  int64_t long_cap = 0;            // vertices whose row is longer than kHead + kShort
   bfsgb::LevelSlot* slot = nullptr;
   bfsgb::LevelLogDev* log = nullptr;
   bfsgb::RunHeader* hdr = nullptr;
+  unsigned long long* arrive = nullptr;  // [kMaxBlocks * 4]
   int32_t* out_scratch = nullptr;  // [2n], for runs with host output buffers
   int grid_blocks = 0;
   int variant = 2;                 // CTAs per SM of the level-loop build in use

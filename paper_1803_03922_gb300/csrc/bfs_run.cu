@@ -70,24 +70,42 @@ __device__ __forceinline__ void set_failed(const BfsParams& p, int code) {
   atomicExch((unsigned*)&p.hdr->err, ((p.epoch & 0x0FFFFFFFu) << 4) | (unsigned)(-code));
 }
 
-// Grid-wide barrier over co-resident CTAs (cooperative launch).  Returns false
-// (uniformly per CTA) if the run failed or the wait passed its deadline.
-__device__ bool grid_sync(const BfsParams& p) {
-  __shared__ int s_ok;
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier over co-resident CTAs (cooperative launch), without a shared
+// atomic counter: every CTA release-stores its own arrival word (epoch-tagged,
+// so words left by earlier runs never match; its low 8 bits carry the OR of the
+// CTA's `flags`), CTA 0's threads acquire-poll all arrival words in parallel,
+// CTA 0's thread 0 runs master(OR of all CTAs' flags) (which may read everything
+// written before the barrier) and release-stores one word that carries the
+// barrier tag and master's 8 result bits; every CTA acquire-polls that word.
+// Every wait has a %globaltimer deadline.  Returns master's bits to every
+// thread of every CTA, or -1 (uniformly per CTA) if the run failed.
+template <class F>
+__device__ int grid_sync(const BfsParams& p, unsigned& seq, F&& master, int flags = 0) {
+  __shared__ int s_res, s_flags;
+  ++seq;
+  const unsigned long long tag =
+      ((unsigned long long)(p.epoch & 0x0FFFFFFFu) << 36) | ((unsigned long long)(seq & 0x0FFFFFFFu) << 8);
+  if (threadIdx.x == 0) s_flags = 0;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned* cnt = &p.hdr->bar_count;
-    unsigned* gen = &p.hdr->bar_gen;
-    unsigned g0 = ld_acquire(gen);
-    __threadfence();
-    if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
-      atomicExch(cnt, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      const unsigned long long t0 = gtimer();
-      while (ld_acquire(gen) == g0) {
+  if (flags) atomicOr(&s_flags, flags);
+  __syncthreads();
+  if (threadIdx.x == 0) st_release64(p.arrive + 4 * blockIdx.x, tag | (unsigned)(s_flags & 0xFF));
+  if (blockIdx.x == 0) {
+    int ok = 1, fl = 0;
+    const unsigned long long t0 = gtimer();
+    for (int t = threadIdx.x; t < (int)gridDim.x && ok; t += blockDim.x) {
+      unsigned long long a;
+      while ((a = ld_acquire64(p.arrive + 4 * t)) < tag) {
         if (run_failed(p)) {
           ok = 0;
           break;
@@ -97,16 +115,39 @@ __device__ bool grid_sync(const BfsParams& p) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(20);
       }
+      fl |= (int)(a & 0xFFu);
     }
-    __threadfence();
-    if (ok && run_failed(p)) ok = 0;
-    s_ok = ok;
+    ok = __syncthreads_and(ok);
+    if (fl) atomicOr(&s_flags, fl);  // every CTA 0 thread has finished with s_flags above
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) st_release64(&p.hdr->release, tag | (unsigned)(master(s_flags) & 0xFF));
+  }
+  if (threadIdx.x == 0) {
+    int res = -1;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+      const unsigned long long r = ld_acquire64(&p.hdr->release);
+      if (r >= tag) {
+        res = (int)(r & 0xFFu);
+        break;
+      }
+      if (run_failed(p)) break;
+      if (gtimer() - t0 > p.timeout_ns) {
+        set_failed(p, BFS_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+    }
+    if (res >= 0 && run_failed(p)) res = -1;
+    s_res = res;
   }
   __syncthreads();
-  return s_ok != 0;
+  return s_res;
 }
+
+__device__ __forceinline__ int no_master(int) { return 0; }
 
 struct Acc {
   unsigned long long nf = 0, mf = 0, edges = 0, scanned = 0, fix = 0;
@@ -218,10 +259,13 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
 //  C: longer rows are finished by the whole warp, one row at a time, 128 entries
 //     per step.
 // On a hit, hit/k are set (k = first-hit position + 1); otherwise k = end - beg.
+// With `defer` (backward levels), long rows are not scanned here: the lane's
+// vertex and row start go to the level's long-row list and hit becomes kDeferred.
+constexpr int kDeferred = -2;
+
 template <bool kFix>
 __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t end, const uint32_t* __restrict__ Ncur,
-                          int& hit, int64_t& k) {
-  constexpr int64_t kShort = 64;
+                          int& hit, int64_t& k, int defer_v = -1, LevelSlot* defer_slot = nullptr) {
   const int lane = lane_id();
   if (more) k = end - beg;
   const bool longrow = more && (end - beg - kHead) > kShort;
@@ -272,6 +316,16 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
     for (int q = 0; q < take; ++q) rem &= rem - 1;
   }
   unsigned lrem = __ballot_sync(kFull, longrow);
+  if (defer_slot && lrem) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&defer_slot->nlong, (unsigned long long)__popc(lrem));
+    base = __shfl_sync(kFull, base, 0);
+    if (longrow) {
+      p.longq[base + __popc(lrem & ((1u << lane) - 1u))] = defer_v;
+      hit = kDeferred;
+    }
+    lrem = 0;
+  }
   while (lrem) {
     const int owner = __ffs(lrem) - 1;
     lrem &= lrem - 1;
@@ -334,14 +388,15 @@ __device__ __forceinline__ void head_probe(const BfsParams& p, const HeadRec& h,
 // hit: loads the row offset and finishes the scan (warp-collective).
 template <bool kFix>
 __device__ __forceinline__ void pull_tail(const BfsParams& p, bool act, int v, int deg,
-                                          const uint32_t* __restrict__ Ncur, int& hit, int& cid, int64_t& k) {
+                                          const uint32_t* __restrict__ Ncur, int& hit, int& cid, int64_t& k,
+                                          LevelSlot* defer_slot = nullptr) {
   const bool more = act && hit < 0 && deg > kHead;
   int64_t beg = 0, end = 0;
   if (more) {
     beg = p.off[v];
     end = beg + deg;
   }
-  pull_rest<kFix>(p, more, beg, end, Ncur, hit, k);
+  pull_rest<kFix>(p, more, beg, end, Ncur, hit, k, v, defer_slot);
   if (more && hit >= 0) cid = p.caller_of[hit];
 }
 
@@ -452,8 +507,33 @@ __device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) 
   }
 }
 
+// Work split: warp w first takes item w; items beyond the first `warps` are
+// handed out from a shared counter in runs of g (about four runs per warp), so
+// warps that drew light items take over the rest without one atomic per item.
+// With no more items than warps the counter is never touched.
+struct WorkCursor {
+  long long it, lim, total, nwarps, g;
+  unsigned long long* ctr;
+  __device__ WorkCursor(long long total_, long long gwarp, long long nwarps_, unsigned long long* ctr_)
+      : it(gwarp), lim(gwarp + 1), total(total_), nwarps(nwarps_), ctr(ctr_) {
+    const long long rest = total_ - nwarps_;
+    g = rest > 0 ? (rest + 4 * nwarps_ - 1) / (4 * nwarps_) : 1;
+  }
+  // next item of this warp, or a value >= total when there is none (warp-uniform)
+  __device__ long long next() {
+    if (it < lim) return it++;
+    if (total <= nwarps) return total;
+    unsigned long long x = 0;
+    if (lane_id() == 0) x = atomicAdd(ctr, (unsigned long long)g);
+    it = nwarps + (long long)__shfl_sync(kFull, x, 0);
+    lim = it + g;
+    return it++;
+  }
+};
+
 // Work items of a forward level: the delegate chunks of F_L, then the normal
-// queue in batches of 32; warp w takes items w, w + warps, ... (no shared counter).
+// queue in batches of 32; warp w takes items w, w + warps, ... (a shared counter
+// measured slower here: the chunks are uniform).
 __device__ void expand_td(const BfsParams& p, int L) {
   const LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sc->qn);
@@ -489,13 +569,101 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
   return pos;
 }
 
-// Items of iw bitmap words (iw = 4..32, larger when few vertices are left);
-// warp w takes items w, w + warps, ...  The unvisited vertices of an item are
-// gathered 32 at a time (lane i takes the i-th one), so a sparse item costs one
-// batch, not one pass per word.  A vertex that finds its parent gets depth and
-// parent; its bit is collected in the warp's shared-memory copy of the item's
-// words, which the warp owns, and each word is written to N once.
-__device__ void expand_bu(const BfsParams& p, int L, long long unvisited, Acc& acc) {
+// One backward item: bitmap words [w0, w0+iw) (iw <= 32) of this warp.  Its
+// unvisited vertices are gathered 32 at a time (lane i takes the i-th one), so a
+// sparse item costs one batch, not one pass per word; two batches are in flight
+// per step.  A vertex that finds its parent gets depth and parent; its bit is
+// collected in the warp's shared copy of the item's words (the warp owns them)
+// and each word is written to N once.
+__device__ bool bu_item(const BfsParams& p, int L, int64_t w0, int iw, unsigned* found, uint32_t* __restrict__ N,
+                        LevelSlot* sc, Acc& acc) {
+  bool deferred = false;
+  const int lane = lane_id();
+  const int64_t W = p.words;
+  const int tail = p.n_ni & 31;
+  const int64_t w = w0 + lane;
+  unsigned vis = kFull;
+  if (lane < iw && w < W) {
+    vis = p.V[w];
+    if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
+  }
+  const unsigned unv = ~vis;
+  const int cnt = __popc(unv);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  const int excl = incl - cnt;
+  // the k-th unvisited vertex of the item: word = first lane whose prefix exceeds k
+  auto locate = [&](int k, int& j, int& bit) {
+    j = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const int t = __shfl_sync(kFull, incl, j + s - 1);
+      if (t <= k) j += s;
+    }
+    const unsigned m = __shfl_sync(kFull, unv, j);
+    const int ex = __shfl_sync(kFull, excl, j);
+    bit = k < total ? nth_set_bit(m, k - ex) : 0;
+  };
+  for (int b = 0; b < total; b += 64) {
+    int jA, jB, bA, bB;
+    locate(b + lane, jA, bA);
+    locate(b + 32 + lane, jB, bB);
+    const bool aA = b + lane < total, aB = b + 32 + lane < total;
+    const int vA = (int)((w0 + jA) * 32 + bA), vB = (int)((w0 + jB) * 32 + bB);
+    const HeadRec hA = head_load(p, aA, vA);
+    const HeadRec hB = head_load(p, aB, vB);
+    int hitA = -1, cidA = -1, hitB = -1, cidB = -1;
+    int64_t kA = 0, kB = 0;
+    if (aA) head_probe<false>(p, hA, nullptr, hitA, cidA, kA);
+    if (aB) head_probe<false>(p, hB, nullptr, hitB, cidB, kB);
+    pull_tail<false>(p, aA, vA, hA.deg, nullptr, hitA, cidA, kA, sc);
+    pull_tail<false>(p, aB, vB, hB.deg, nullptr, hitB, cidB, kB, sc);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      deferred |= (q ? aB : aA) && (q ? hitB : hitA) == kDeferred;
+      const bool act = (q ? aB : aA) && (q ? hitB : hitA) != kDeferred;
+      const int hit = q ? hitB : hitA;
+      const int v = q ? vB : vA;
+      const int j = q ? jB : jA;
+      // lanes of one batch that share a word are adjacent: OR their bits
+      const unsigned fbit = (act && hit >= 0) ? (1u << (q ? bB : bA)) : 0u;
+      const unsigned grp = __match_any_sync(kFull, (unsigned)j);
+      const unsigned orb = __reduce_or_sync(grp, fbit);
+      if (orb && lane == __ffs(grp) - 1) found[j] |= orb;
+      if (!act) continue;
+      acc.scanned += 1;
+      acc.edges += (unsigned long long)(q ? kB : kA);
+      if (hit >= 0) {
+        p.parent_i[v] = q ? cidB : cidA;
+        p.depth_i[v] = L + 1;
+        acc.nf += 1;
+        acc.mf += (unsigned long long)(q ? hB.deg : hA.deg);
+      }
+    }
+    __syncwarp();
+  }
+  if (lane < iw) {
+    const unsigned f = found[lane];
+    if (f) {
+      atomicOr(N + w0 + lane, f);  // deferred rows of other warps may add bits to this word
+      found[lane] = 0u;
+    }
+  }
+  __syncwarp();
+  return deferred;
+}
+
+// A backward level: items of iw bitmap words (iw = 4..32, larger when few
+// vertices are left), split statically; rows still unsettled after kHead +
+// kShort entries are deferred to the level's long-row list, which all warps then
+// drain with dynamic hand-out, one row per warp and 128-bit loads, so that long
+// scans spread over the grid instead of stalling the warp that met them.
+__device__ bool expand_bu(const BfsParams& p, int L, int iw, Acc& acc) {
   __shared__ unsigned s_found[kWarpsPerBlock][32];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
@@ -503,91 +671,43 @@ __device__ void expand_bu(const BfsParams& p, int L, long long unvisited, Acc& a
   found[lane] = 0u;
   __syncwarp();
   const int64_t W = p.words;
-  // about 64 unvisited vertices per item: iw ~ 2 n_ni / unvisited words
-  int iw = 4;
-  while (iw < 32 && (long long)iw * unvisited < 2LL * p.n_ni) iw <<= 1;
-  const int64_t items = (W + iw - 1) / iw;
-  const int tail = p.n_ni & 31;
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t it = gwarp; it < items; it += nwarps) {
-    const int64_t w = it * iw + lane;
-    unsigned vis = kFull;
-    if (lane < iw && w < W) {
-      vis = p.V[w];
-      if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
-    }
-    const unsigned unv = ~vis;
-    const int cnt = __popc(unv);
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - cnt;
-    // the k-th unvisited vertex of the item: word = first lane whose prefix exceeds k
-    auto locate = [&](int k, int64_t& word, int& bit) {
-      int j = 0;
-#pragma unroll
-      for (int s = 16; s >= 1; s >>= 1) {
-        const int t = __shfl_sync(kFull, incl, j + s - 1);
-        if (t <= k) j += s;
-      }
-      const unsigned m = __shfl_sync(kFull, unv, j);
-      const int ex = __shfl_sync(kFull, excl, j);
-      bit = k < total ? nth_set_bit(m, k - ex) : 0;
-      word = it * iw + j;
-    };
-    // two batches of 32 vertices per step: both head records are loaded, and
-    // all eight head probes issued, before either batch waits on a result
-    for (int b = 0; b < total; b += 64) {
-      int64_t wA, wB;
-      int bA, bB;
-      locate(b + lane, wA, bA);
-      locate(b + 32 + lane, wB, bB);
-      const bool aA = b + lane < total, aB = b + 32 + lane < total;
-      const int vA = (int)(wA * 32 + bA), vB = (int)(wB * 32 + bB);
-      const HeadRec hA = head_load(p, aA, vA);
-      const HeadRec hB = head_load(p, aB, vB);
-      int hitA = -1, cidA = -1, hitB = -1, cidB = -1;
-      int64_t kA = 0, kB = 0;
-      if (aA) head_probe<false>(p, hA, nullptr, hitA, cidA, kA);
-      if (aB) head_probe<false>(p, hB, nullptr, hitB, cidB, kB);
-      pull_tail<false>(p, aA, vA, hA.deg, nullptr, hitA, cidA, kA);
-      pull_tail<false>(p, aB, vB, hB.deg, nullptr, hitB, cidB, kB);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const bool act = q ? aB : aA;
-        const int hit = q ? hitB : hitA;
-        const int v = q ? vB : vA;
-        const int64_t word = q ? wB : wA;
-        // lanes of one batch that share a word are adjacent: OR their bits
-        const unsigned fbit = (act && hit >= 0) ? (1u << (q ? bB : bA)) : 0u;
-        const unsigned grp = __match_any_sync(kFull, (unsigned)(word - it * iw));
-        const unsigned orb = __reduce_or_sync(grp, fbit);
-        if (orb && lane == __ffs(grp) - 1) found[word - it * iw] |= orb;
-        if (!act) continue;
-        acc.scanned += 1;
-        acc.edges += (unsigned long long)(q ? kB : kA);
-        if (hit >= 0) {
-          p.parent_i[v] = q ? cidB : cidA;
-          p.depth_i[v] = L + 1;
-          acc.nf += 1;
-          acc.mf += (unsigned long long)(q ? hB.deg : hA.deg);
-        }
-      }
-      __syncwarp();
-    }
-    if (lane < iw) {
-      const unsigned f = found[lane];
-      if (f) {
-        N[it * iw + lane] = f;
-        found[lane] = 0u;
+  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  const int64_t nitems = (W + iw - 1) / iw;
+  bool deferred = false;
+  for (int64_t it = gwarp; it < nitems; it += nwarps) deferred |= bu_item(p, L, it * iw, iw, found, N, sc, acc);
+  return deferred;
+}
+
+// Second half of a backward level, between two grid barriers (so the long-row
+// list is complete and V is still read-only): all warps take deferred rows from
+// a shared counter in runs and scan them with 128-bit loads; a vertex found here
+// sets its bit in N with an atomic.
+__device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
+  LevelSlot* sc = p.slot + (L & (kSlots - 1));
+  uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+  const long long nl = (long long)__ldcg(&sc->nlong);
+  if (nl == 0) return;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  WorkCursor wc(nl, gwarp, nwarps, &sc->work2);
+  for (long long e = wc.next(); e < nl; e = wc.next()) {
+    const int v = p.longq[e];
+    const int64_t rb = p.off[v], re = rb + p.deg[v];
+    int64_t kv;
+    const int hit = warp_scan<false>(p, rb, rb + kHead, re, nullptr, kv);
+    if (lane_id() == 0) {
+      acc.scanned += 1;
+      acc.edges += (unsigned long long)kv;
+      if (hit >= 0) {
+        p.parent_i[v] = p.caller_of[hit];
+        p.depth_i[v] = L + 1;
+        atomicOr(Ncur + (v >> 5), 1u << (v & 31));
+        acc.nf += 1;
+        acc.mf += (unsigned long long)(re - rb);
       }
     }
-    __syncwarp();
   }
 }
 
@@ -698,7 +818,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
   }
 }
 
-// V |= Ncur and Nclr = 0, 4 words per thread.
+// V |= Ncur and Nclr = 0, 4 words per thread (the level end of a backward level).
 __device__ void merge_bitmaps(const BfsParams& p, const uint32_t* __restrict__ Ncur, uint32_t* __restrict__ Nclr) {
   const int64_t W4 = (p.words + 3) / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -783,35 +903,31 @@ __device__ int decide(const BfsParams& p, int L1, int cur, unsigned long long nf
 
 __device__ void run_body(const BfsParams& p);
 
-// Every CTA passes here on exit, normal or not; the last one leaves the barrier
-// counter at zero for the next run.
-__device__ void block_exit(const BfsParams& p) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&p.hdr->exited, 1u) == gridDim.x - 1) {
-      atomicExch(&p.hdr->bar_count, 0u);
-      atomicExch(&p.hdr->exited, 0u);
-      __threadfence();
-    }
-  }
-}
 
 // Two builds of the same kernel: 2 CTAs of 512 threads per SM (64 registers) or
 // 3 (40 registers, some spilled to local memory).
 template <int kMinBlocks>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) bfs_level_loop(BfsParams p) {
   run_body(p);
-  block_exit(p);
+}
+
+// Bits a barrier's master hands to every CTA.
+constexpr int kBitBackward = 1, kBitDone = 2, kBitConvert = 4, kBitDrain = 8;
+__device__ __forceinline__ int iw_code(long long unvisited, int n_ni) {
+  int c = 0;  // item width 4 << c words: about 64 unvisited vertices per backward item
+  while (c < 3 && (long long)(4 << c) * unvisited < 2LL * n_ni) ++c;
+  return c << 4;
 }
 
 __device__ void run_body(const BfsParams& p) {
-  __shared__ int s_dir, s_done, s_conv;
+  // state of the direction decision, kept by CTA 0 (the barriers' master)
   __shared__ long long s_mu, s_unv;
-  __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te;
+  __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te, s_tnf;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+  const bool trace = (p.tuning & 2) != 0;
+  unsigned seq = 0;
   Acc acc;
 
   // ---- init: clear bitmaps, seed the source ----
@@ -850,7 +966,10 @@ __device__ void run_body(const BfsParams& p) {
   unsigned long long src_deg = 0;
   if (src_in) src_deg = (unsigned long long)(p.off[src_i + 1] - p.off[src_i]);
   if (leader) {
-    for (int k = 0; k < kSlots; ++k) p.slot[k] = LevelSlot();
+    for (int k = 0; k < kSlots; ++k) {
+      p.slot[k] = LevelSlot();
+      p.slot[k].t_first = ~0ull;
+    }
     p.hdr->t0 = gtimer();
     if (src_in) {
       p.depth_i[src_i] = 0;
@@ -866,48 +985,63 @@ __device__ void run_body(const BfsParams& p) {
         p.slot[0].nch = (unsigned long long)nch;
       }
     }
-  }
-  if (threadIdx.x == 0) {
-    s_done = src_in ? 0 : 1;
     s_mu = (long long)p.nnz - (long long)src_deg;
     s_unv = (long long)p.n_ni - (src_in ? 1 : 0);
     s_prev_nf = 1;
     s_reach_e = src_deg;
     s_reach_v = 1;
-    s_dir = decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv);
-    s_conv = 0;
   }
   if (p.test_skip_barrier && blockIdx.x == 0) return;  // the others' bounded wait must expire
-  if (!grid_sync(p)) return;
+  int bits = grid_sync(p, seq, [&](int) {
+    return (src_in ? 0 : kBitDone) | (decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv) ? kBitBackward : 0) |
+           iw_code(s_unv, p.n_ni);
+  });
+  if (bits < 0) return;
 
   const unsigned long long t_start = gtimer();
   if (leader) p.hdr->t_init = t_start;
   int L = 0;
-  while (!s_done) {
+  while (!(bits & kBitDone)) {
     // Bounds against a run that does not end: at most n_ni+1 levels, and the
     // run's deadline.  A failure set here ends every CTA at its next barrier.
     if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
       set_failed(p, BFS_ERR_TIMEOUT);
-    const int dir = s_dir;
-    const long long s_unv_level = s_unv;
+    const int dir = (bits & kBitBackward) ? 1 : 0;
+    const bool conv = (bits & kBitConvert) != 0;
+    const int iw = 4 << ((bits >> 4) & 3);
     LevelSlot* sc = p.slot + (L & (kSlots - 1));
     LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
     uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
     uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
-    if (s_conv) {
+    if (conv) {
       // F_L is the bitmap of the previous (backward) level's discoveries.
       frontier_from_bitmap(p, Noth, nullptr, (L & 1) ? p.Q1 : p.Q0, (L & 1) ? p.CL1 : p.CL0, sc, false, false, 0,
                            acc);
-      if (!grid_sync(p)) return;
+      if (grid_sync(p, seq, no_master) < 0) return;
     }
     if (leader) s_tb = gtimer();
+    bool deferred = false;
     if (dir == 0) {
       expand_td(p, L);
     } else {
-      expand_bu(p, L, s_unv_level, acc);
+      deferred = expand_bu(p, L, iw, acc);
       flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
     }
-    if (!grid_sync(p)) return;
+    if (trace) {  // spread of the CTAs' finishing times
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const unsigned long long t = gtimer();
+        atomicMin(&sc->t_first, t);
+        atomicMax(&sc->t_last, t);
+      }
+    }
+    const int eb = grid_sync(p, seq, [&](int fl) { return fl & kBitDrain; }, deferred ? kBitDrain : 0);
+    if (eb < 0) return;
+    if (eb & kBitDrain) {
+      drain_long_rows(p, L, acc);
+      flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
+      if (grid_sync(p, seq, no_master) < 0) return;
+    }
     if (leader) s_te = gtimer();
     if (dir == 0) {
       // merge, then the next frontier's queues, depths and counts
@@ -915,46 +1049,47 @@ __device__ void run_body(const BfsParams& p) {
                            acc);
       flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
       if (p.td_parent == BFS_TD_PARENT_PULL) {
-        if (!grid_sync(p)) return;  // the queues of F_{L+1} are complete
+        if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
         pull_parents(p, L, acc);
         flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
       }
     } else {
       merge_bitmaps(p, Ncur, Noth);
     }
-    if (leader) p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
-    if (!grid_sync(p)) return;
-    if (threadIdx.x == 0) {
+    if (leader) {
+      p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+      p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
+    }
+    bits = grid_sync(p, seq, [&](int) {
       const unsigned long long nf = __ldcg(&sn->n_f), mf = __ldcg(&sn->m_f);
-      if (leader && L < BFS_LOG_LEVELS) {
-        LevelLogDev& lg = p.log[L];
-        lg.dir = dir;
-        lg.converted = s_conv;
-        lg.n_f = __ldcg(&sc->n_f);
-        lg.m_f = __ldcg(&sc->m_f);
-        lg.scanned = __ldcg(&sc->scanned);
-        lg.edges = dir == 0 ? __ldcg(&sc->m_f) : __ldcg(&sc->edges);
-        lg.fix_edges = __ldcg(&sc->fix_edges);
-        lg.found = nf;
-        lg.qn = __ldcg(&sc->qn);
-        lg.t_begin = s_tb;
-        lg.t_expand = s_te;
-        lg.t_end = gtimer();
-      }
+      s_tnf = nf;
       s_mu -= (long long)mf;
       s_unv -= (long long)nf;
       s_reach_e += mf;
       s_reach_v += nf;
-      if (nf == 0) {
-        s_done = 1;
-      } else {
-        const int nd = decide(p, L + 1, dir, nf, mf, s_prev_nf, s_mu, s_unv);
-        s_conv = (nd == 0 && dir == 1) ? 1 : 0;
-        s_dir = nd;
-        s_prev_nf = nf;
-      }
+      if (nf == 0) return kBitDone;
+      const int nd = decide(p, L + 1, dir, nf, mf, s_prev_nf, s_mu, s_unv);
+      s_prev_nf = nf;
+      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni);
+    });
+    if (bits < 0) return;
+    if (leader && L < BFS_LOG_LEVELS) {  // the level's log, after the release (slot L stays intact until L+2)
+      LevelLogDev& lg = p.log[L];
+      lg.t_end = gtimer();
+      lg.dir = dir;
+      lg.converted = conv ? 1 : 0;
+      lg.n_f = __ldcg(&sc->n_f);
+      lg.m_f = __ldcg(&sc->m_f);
+      lg.scanned = __ldcg(&sc->scanned);
+      lg.edges = dir == 0 ? __ldcg(&sc->m_f) : __ldcg(&sc->edges);
+      lg.fix_edges = __ldcg(&sc->fix_edges);
+      lg.found = s_tnf;
+      lg.qn = __ldcg(&sc->qn);
+      lg.t_begin = s_tb;
+      lg.t_expand = s_te;
+      lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
+      lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
     }
-    __syncthreads();
     ++L;
   }
 
@@ -998,7 +1133,6 @@ __device__ void run_body(const BfsParams& p) {
   }
 }
 
-
 }  // namespace
 
 int configure_run(bfs_graph* g) {
@@ -1016,6 +1150,7 @@ int configure_run(bfs_graph* g) {
   const int want = per_sm < variant ? per_sm : variant;
   g->variant = variant;
   g->grid_blocks = sms * want;
+  if (g->grid_blocks > kMaxBlocks) g->grid_blocks = kMaxBlocks;
   return BFS_OK;
 }
 
@@ -1027,6 +1162,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.internal_of = g->internal_of;
   p.head = g->head;
   p.deg = g->deg;
+  p.longq = g->longq;
   p.V = g->V;
   p.N0 = g->N0;
   p.N1 = g->N1;
@@ -1039,6 +1175,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.slot = g->slot;
   p.log = g->log;
   p.hdr = g->hdr;
+  p.arrive = g->arrive;
   p.out_depth = out_depth;
   p.out_parent = out_parent;
   p.nnz = g->nnz;
@@ -1061,6 +1198,11 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.tuning = g->opt.tuning;
   p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
+  if (p.epoch == 1) {  // first run, or the run counter wrapped: barrier words must restart below any tag
+    cudaError_t e0 = cudaMemsetAsync(g->arrive, 0, sizeof(unsigned long long) * kMaxBlocks * 4, s);
+    if (e0 == cudaSuccess) e0 = cudaMemsetAsync(&g->hdr->release, 0, sizeof(unsigned long long), s);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "reset barrier words");
+  }
   void* args[] = {&p};
   const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3> : (const void*)bfs_level_loop<2>;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid_blocks), dim3(kThreads), args, 0, s);

@@ -110,17 +110,20 @@ __global__ void k_scatter_cols(const uint64_t* __restrict__ keys, int64_t M, con
   if (threadIdx.x < 4 && s[threadIdx.x]) atomicAdd(&sub[threadIdx.x], s[threadIdx.x]);
 }
 
-// Largest degree and the chunk-list capacity sum_{v<d} ceil(deg(v)/kChunk).
+// Largest degree, the chunk-list capacity sum_{v<d} ceil(deg(v)/kChunk), and the
+// number of rows longer than kHead + kShort (capacity of the long-row list).
 __global__ void k_degree_stats(const int64_t* __restrict__ off, int32_t n_ni, int32_t d,
-                               unsigned long long* __restrict__ out /* [0]=max deg, [1]=chunks */) {
-  unsigned long long mx = 0, ch = 0;
+                               unsigned long long* __restrict__ out /* [0]=max deg, [1]=chunks, [2]=long rows */) {
+  unsigned long long mx = 0, ch = 0, lg = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_ni; v += (int64_t)gridDim.x * blockDim.x) {
     int64_t deg = off[v + 1] - off[v];
     mx = deg > (int64_t)mx ? (unsigned long long)deg : mx;
     if (v < d) ch += (deg + kChunk - 1) / kChunk;
+    if (deg > kHead + kShort) lg += 1;
   }
   atomicMax(&out[0], mx);
   if (ch) atomicAdd(&out[1], ch);
+  if (lg) atomicAdd(&out[2], lg);
 }
 
 // Per-vertex head record: the first kHead row entries (internal ids, -1 past the
@@ -333,6 +336,7 @@ int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, co
   for (int j = 0; j < 4; ++j) g->sub[j] = (int64_t)hs[j];
   g->max_deg = (int64_t)hs[4];
   g->cl_cap = (int64_t)hs[5] + 1;
+  g->long_cap = (int64_t)hs[6] + 1;
   g->device_bytes = dev_bytes;
   return BFS_OK;
 }
