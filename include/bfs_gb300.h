@@ -162,6 +162,51 @@ typedef struct bfs_stats {
 int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* parent, bfs_stats* stats,
             struct CUstream_st* stream);
 
+/* ---- Batched form: up to 64 queries per launch (64-lane bitset multi-source BFS). ----
+ * Not in the paper, which runs one source at a time; the per-query result is the
+ * same hop distance and canonical parent as bfs_run, with uint8 depth. */
+typedef struct bfs_batch bfs_batch;
+
+#define BFS_BATCH_LOG_LEVELS 64
+
+typedef struct bfs_batch_level {
+  int32_t direction;          /* 0 forward, 1 backward */
+  int32_t pad;
+  int64_t frontier_vertices;  /* vertices in the union of the queries' frontiers */
+  int64_t frontier_edges;     /* their degree sum */
+  int64_t pairs;              /* (query, vertex) pairs in the frontier */
+  uint64_t t_begin_ns, t_expand_ns, t_end_ns;
+} bfs_batch_level;
+
+typedef struct bfs_batch_stats {
+  int32_t levels;          /* levels run by the batch (max over its queries of max depth + 1) */
+  int32_t logged_levels;   /* min(levels, BFS_BATCH_LOG_LEVELS) */
+  int64_t pairs_reached;   /* (query, vertex) pairs reached, sources excluded */
+  int64_t traversed_edges; /* sum over the queries of the traversed component's undirected edges */
+  uint64_t device_ns;      /* %globaltimer span of the launch */
+  uint64_t setup_ns;       /* part of device_ns before level 0 */
+  uint64_t result_ns;      /* part of device_ns writing the results */
+  bfs_batch_level level[BFS_BATCH_LOG_LEVELS];
+} bfs_batch_stats;
+
+/* Device state for batches on graph g (about 8*4 + 64 (+256 with parents) bytes per
+ * non-isolated vertex).  One batch at a time per context; several contexts on
+ * different streams may run concurrently.  The graph must outlive the context. */
+int bfs_batch_create(const bfs_graph* g, int32_t with_parents, bfs_batch** out);
+
+/* k (1..64) queries from sources[0..k) (host array of caller ids; repeats allowed).
+ * depth[k*n] uint8 row-major by query (255 = unreached); parent[k*n] int32 (may be
+ * NULL; requires a context created with parents); both device or both host.  Device
+ * buffers: asynchronous on `stream` (status via bfs_batch_wait or stats); host
+ * buffers or stats: synchronizes.  BFS_ERR_OVERFLOW when a depth would exceed 254. */
+int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, uint8_t* depth, int32_t* parent,
+                  bfs_batch_stats* stats, struct CUstream_st* stream);
+
+/* Synchronizes `stream`; status of the context's most recent batch. */
+int bfs_batch_wait(bfs_batch* b, struct CUstream_st* stream);
+
+void bfs_batch_free(bfs_batch* b);
+
 /* Synchronizes `stream` and returns the device-side status of the graph's most
  * recent run: BFS_OK, or BFS_ERR_TIMEOUT when a bounded wait expired (runs with
  * device buffers and no stats do not report it themselves). */
@@ -195,8 +240,9 @@ void bfs_free(bfs_graph* g);
 const char* bfs_last_error(void);
 
 /* sizeof of the ABI structs, for bindings to check their layouts:
- * sizes[0] bfs_options, [1] bfs_graph_info, [2] bfs_level_log, [3] bfs_stats. */
-void bfs_abi_sizes(int64_t sizes[4]);
+ * sizes[0] bfs_options, [1] bfs_graph_info, [2] bfs_level_log, [3] bfs_stats,
+ * [4] bfs_batch_stats. */
+void bfs_abi_sizes(int64_t sizes[5]);
 
 #ifdef __cplusplus
 }

@@ -70,6 +70,20 @@ class bfs_stats(ctypes.Structure):
                 ("level", bfs_level_log * BFS_LOG_LEVELS)]
 
 
+BFS_BATCH_LOG_LEVELS = 64
+
+
+class bfs_batch_level(ctypes.Structure):
+    _fields_ = [("direction", c_i32), ("pad", c_i32), ("frontier_vertices", c_i64), ("frontier_edges", c_i64),
+                ("pairs", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64)]
+
+
+class bfs_batch_stats(ctypes.Structure):
+    _fields_ = [("levels", c_i32), ("logged_levels", c_i32), ("pairs_reached", c_i64), ("traversed_edges", c_i64),
+                ("device_ns", c_u64), ("setup_ns", c_u64), ("result_ns", c_u64),
+                ("level", bfs_batch_level * BFS_BATCH_LOG_LEVELS)]
+
+
 class BfsError(RuntimeError):
     def __init__(self, code, message):
         super().__init__("bfs error %d: %s" % (code, message))
@@ -101,11 +115,16 @@ def _load():
     lib.bfs_free.restype = None
     lib.bfs_last_error.restype = ctypes.c_char_p
     lib.bfs_last_error.argtypes = []
-    lib.bfs_abi_sizes.argtypes = [ctypes.POINTER(c_i64 * 4)]
+    lib.bfs_batch_create.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp)]
+    lib.bfs_run_batch.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(bfs_batch_stats), c_vp]
+    lib.bfs_batch_wait.argtypes = [c_vp, c_vp]
+    lib.bfs_batch_free.argtypes = [c_vp]
+    lib.bfs_batch_free.restype = None
+    lib.bfs_abi_sizes.argtypes = [ctypes.POINTER(c_i64 * 5)]
     lib.bfs_abi_sizes.restype = None
-    sizes = (c_i64 * 4)()
+    sizes = (c_i64 * 5)()
     lib.bfs_abi_sizes(ctypes.byref(sizes))
-    want = [ctypes.sizeof(t) for t in (bfs_options, bfs_graph_info, bfs_level_log, bfs_stats)]
+    want = [ctypes.sizeof(t) for t in (bfs_options, bfs_graph_info, bfs_level_log, bfs_stats, bfs_batch_stats)]
     if list(sizes) != want:
         raise ImportError("ABI struct sizes differ: library %s, binding %s" % (list(sizes), want))
     _lib = lib
@@ -218,6 +237,29 @@ def bfs_run_static(row_off, col, n: int, source: int, depth, parent, stream=None
                                   _stream(stream)))
 
 
+def bfs_batch_create(g, with_parents: bool = True):
+    h = c_vp()
+    _check(_load().bfs_batch_create(g, 1 if with_parents else 0, ctypes.byref(h)))
+    return h
+
+
+def bfs_run_batch(b, sources, depth, parent=None, stats: bfs_batch_stats | None = None, stream=None):
+    """sources: host int32 array (1..64 caller ids); depth uint8 [k*n], parent int32 [k*n]
+    (or None), both device tensors or both host arrays/pinned tensors."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    _check(_load().bfs_run_batch(b, _ptr(src), src.size, _ptr(depth), _ptr(parent),
+                                 ctypes.byref(stats) if stats is not None else None, _stream(stream)))
+
+
+def bfs_batch_wait(b, stream=None):
+    _check(_load().bfs_batch_wait(b, _stream(stream)))
+
+
+def bfs_batch_free(b):
+    if b:
+        _load().bfs_batch_free(b)
+
+
 def bfs_free(g):
     if g:
         _load().bfs_free(g)
@@ -272,6 +314,44 @@ class Graph:
     def close(self):
         if getattr(self, "_h", None):
             bfs_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Device state for 64-lane batches of queries on a Graph."""
+
+    def __init__(self, graph: "Graph", with_parents: bool = True):
+        self.graph = graph
+        self.with_parents = with_parents
+        self._h = bfs_batch_create(graph.handle, with_parents)
+
+    def run(self, sources, depth=None, parent=None, stats: bool = False, stream=None):
+        """Runs len(sources) <= 64 queries; returns (depth [k, n] uint8, parent [k, n] int32 or
+        None[, stats]) as CUDA tensors (allocated when not given)."""
+        import torch
+
+        k = len(sources)
+        n = self.graph.n
+        if depth is None:
+            depth = torch.empty((k, n), dtype=torch.uint8, device="cuda")
+        if parent is None and self.with_parents:
+            parent = torch.empty((k, n), dtype=torch.int32, device="cuda")
+        st = bfs_batch_stats() if stats else None
+        bfs_run_batch(self._h, sources, depth, parent, st, stream)
+        return (depth, parent, st) if stats else (depth, parent)
+
+    def wait(self, stream=None):
+        bfs_batch_wait(self._h, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            bfs_batch_free(self._h)
             self._h = None
 
     def __del__(self):

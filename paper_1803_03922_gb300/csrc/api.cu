@@ -345,9 +345,10 @@ extern "C" void bfs_free(bfs_graph* g) {
 
 extern "C" const char* bfs_last_error(void) { return t_error.c_str(); }
 
-extern "C" void bfs_abi_sizes(int64_t sizes[4]) {
+extern "C" void bfs_abi_sizes(int64_t sizes[5]) {
   sizes[0] = (int64_t)sizeof(bfs_options);
   sizes[1] = (int64_t)sizeof(bfs_graph_info);
   sizes[2] = (int64_t)sizeof(bfs_level_log);
   sizes[3] = (int64_t)sizeof(bfs_stats);
+  sizes[4] = (int64_t)sizeof(bfs_batch_stats);
 }

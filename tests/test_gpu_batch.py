@@ -1,0 +1,112 @@
+"""Batched form (64-lane bitset multi-source BFS) vs the oracle's uint8 batched
+BFS, bit-exact: depth (255 = unreached) and canonical parent for every query."""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests.gpu_util import assert_same, gpu_graph, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_check(og, g, sources, with_parents=True, host=False):
+    torch = need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    b = bfs.Batch(g, with_parents=with_parents)
+    want_d, want_p = og.bfs_batch_u8(sources)
+    if host:
+        k, n = len(sources), g.n
+        d = np.empty((k, n), np.uint8)
+        p = np.empty((k, n), np.int32) if with_parents else None
+        bfs.bfs_run_batch(b._h, sources, d, p)
+    else:
+        d, p, st = b.run(sources, stats=True)
+        d = d.cpu().numpy()
+        p = p.cpu().numpy() if with_parents else None
+        assert st.pairs_reached == int((want_d != 255).sum()) - sum(
+            1 for s in sources if True)  # every source lane reaches its source at depth 0
+    for j, s in enumerate(sources):
+        assert_same(d[j], want_d[j], "depth of query %d (source %d)" % (j, s))
+        if with_parents:
+            assert_same(p[j], want_p[j], "parent of query %d (source %d)" % (j, s))
+    b.close()
+
+
+def _closed():
+    R, C = 9, 13
+    grid = []
+    for r in range(R):
+        for c in range(C):
+            if r + 1 < R:
+                grid.append((r * C + c, (r + 1) * C + c))
+            if c + 1 < C:
+                grid.append((r * C + c + 1, r * C + c))
+    return {
+        "path": (50, [(i, i + 1) for i in range(49)]),
+        "star": (70, [(13, v) for v in range(70) if v != 13]),
+        "grid": (R * C, grid),
+        "cycle": (66, [(i, (i + 1) % 66) for i in range(66)]),
+        "complete": (30, list(itertools.combinations(range(30), 2))),
+        "components": (75, [(0, 1), (1, 2), (40, 41), (41, 42), (42, 43), (70, 71)]),
+    }
+
+
+@pytest.mark.parametrize("name", list(_closed().keys()))
+@pytest.mark.parametrize("th", [0, 3, 64])
+def test_batch_closed_forms(name, th):
+    n, e = _closed()[name]
+    e = np.asarray(e, np.int32)
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th)
+    rng = np.random.default_rng(n + th)
+    sources = rng.integers(0, n, 64)
+    _batch_check(og, g, sources)
+    _batch_check(og, g, sources[:5])  # a partial batch
+    _batch_check(og, g, [int(sources[0])] * 3 + [n - 1])  # repeated sources
+
+
+def test_batch_random_graphs():
+    rng = np.random.default_rng(77)
+    for trial in range(20):
+        n = int(rng.integers(2, 600))
+        m = int(rng.integers(0, 8 * n))
+        src = rng.integers(0, n, m).astype(np.int32)
+        dst = rng.integers(0, n, m).astype(np.int32)
+        og = oracle.Graph(n, src, dst)
+        g = gpu_graph(n, src, dst, th=int(rng.choice([0, 4, 16, 10**9])))
+        k = int(rng.integers(1, 65))
+        _batch_check(og, g, rng.integers(0, n, k), with_parents=bool(trial % 4))
+
+
+def test_batch_rmat16_64_sources():
+    scale = 16
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=16)
+    og = oracle.Graph(n, src, dst)
+    mask = graphgen.nonisolated_mask_host(n, src, dst)
+    sources = graphgen.sample_sources(mask, 64, seed=1601)
+    for th in (0, 64, 10**9):
+        g = gpu_graph(n, src, dst, th=th)
+        _batch_check(og, g, sources)
+    _batch_check(og, g, sources[:33], host=True)
+
+
+def test_batch_isolated_and_overflow():
+    torch = need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    e = np.array([(i, i + 1) for i in range(299)], np.int32)  # path: depth 299 from an end
+    og = oracle.Graph(302, e[:, 0], e[:, 1])
+    g = gpu_graph(302, e[:, 0], e[:, 1], th=8)
+    _batch_check(og, g, [150, 301, 100])  # 301 is isolated; depths <= 200
+    b = bfs.Batch(g)
+    with pytest.raises(bfs.BfsError) as ex:
+        b.run([150, 0], stats=True)
+    assert ex.value.code == bfs.BFS_ERR_OVERFLOW
+    d, p, st = b.run([150], stats=True)  # the context stays usable
+    dn = d.cpu().numpy()
+    assert int(dn[dn != 255].max()) == 150 and st.levels == 151
