@@ -353,6 +353,214 @@ def run_reference(args, w, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---- batched form and serving loop ----------------------------------------------------------
+
+SERVE_GRAPHS = [
+    ("rmat18", dict(kind="rmat", scale=18, th=64, seed=18, src_seed=1801)),
+    ("rmat20", dict(kind="rmat", scale=20, th=64, seed=20, src_seed=2001)),
+    ("rmat22", dict(kind="rmat", scale=22, th=64, seed=22, src_seed=2201)),
+    ("rmat24", dict(kind="rmat", scale=24, th=64, seed=24, src_seed=2401)),
+    ("er22", dict(kind="er", scale=22, avgdeg=16, th=64, seed=122, src_seed=12201)),
+]
+SERVE_RATES = (1000, 4000, 16000)
+SERVE_SOURCES = 1024
+SERVE_POOL = 160  # output buffer pairs per graph (queries outstanding before the client waits)
+
+
+def build_served_graph(w):
+    import torch
+
+    import graphgen
+    import paper_1803_03922_gb300 as bfs
+
+    n = 1 << w["scale"]
+    src, dst = make_edges_device(w)
+    mask = graphgen.nonisolated_mask_device(n, src, dst).cpu().numpy()
+    sources = graphgen.sample_sources(mask, SERVE_SOURCES, seed=w["src_seed"])
+    g = bfs.Graph(src, dst, n, th=w["th"])
+    del src, dst
+    torch.cuda.empty_cache()
+    return g, sources
+
+
+def batched_vs_single(g, sources, batches=8):
+    """64-lane batches against one query at a time on the same graph and sources:
+    queries/s from CUDA events over `batches` x 64 queries, parents included."""
+    import torch
+
+    import paper_1803_03922_gb300 as bfs
+
+    n = g.n
+    out = {}
+    for with_par in (True, False):
+        b = bfs.Batch(g, with_parents=with_par)
+        depth = torch.empty((64, n), dtype=torch.uint8, device="cuda")
+        parent = torch.empty((64, n), dtype=torch.int32, device="cuda") if with_par else None
+        for i in range(2):
+            b.run(sources[64 * i:64 * (i + 1)], depth, parent)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(batches):
+            b.run(sources[64 * i:64 * (i + 1)], depth, parent)
+        e1.record()
+        torch.cuda.synchronize()
+        b.wait()
+        ms = e0.elapsed_time(e1)
+        out["batched_qps" if with_par else "batched_depth_only_qps"] = 64 * batches / ms * 1e3
+        out["ms_per_batch" if with_par else "ms_per_batch_depth_only"] = ms / batches
+        b.close()
+        del depth, parent
+        torch.cuda.empty_cache()
+    d1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    p1 = torch.empty(n, dtype=torch.int32, device="cuda")
+    for s in sources[:4]:
+        g.run(int(s), d1, p1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in sources[:64 * batches]:
+        g.run(int(s), d1, p1)
+    e1.record()
+    torch.cuda.synchronize()
+    g.wait()
+    ms = e0.elapsed_time(e1)
+    out["single_qps"] = 64 * batches / ms * 1e3
+    out["speedup"] = out["batched_qps"] / out["single_qps"]
+    return out
+
+
+def serve_trace(rate, count, n_graphs, n_sources, seed):
+    """Open-loop Poisson arrivals: (offset ns, graph id, source index), graphs uniform."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1e9 / rate, count)
+    offs = np.cumsum(gaps).astype(np.int64)
+    gids = rng.integers(0, n_graphs, count)
+    idx = rng.integers(0, n_sources, count)
+    return list(zip(offs.tolist(), gids.tolist(), idx.tolist()))
+
+
+def latency_summary(lat_ns, t_first, t_last, count):
+    import numpy as np
+
+    lat = np.asarray(lat_ns, dtype=np.float64) / 1e6
+    span = (t_last - t_first) / 1e9
+    return {"queries": count, "qps": count / span if span > 0 else None,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean())}
+
+
+def serve_open_loop(srv, graphs, sources, pools, trace):
+    """Submits each query at its arrival time (through bfs_server_submit with that
+    arrival stamp) and collects completions; returns the latency summary."""
+    import paper_1803_03922_gb300 as bfs
+
+    h = srv._h
+    t0 = bfs.bfs_server_now_ns() + 2_000_000
+    i, outstanding, lat, bad = 0, {}, [], 0
+    t_last = t0
+    while i < len(trace) or outstanding:
+        now = bfs.bfs_server_now_ns()
+        while i < len(trace) and t0 + trace[i][0] <= now:
+            off, gid, si = trace[i]
+            if not pools[gid]:
+                break  # the client has no free result buffer for this graph: wait
+            d, p = pools[gid].pop()
+            t = bfs.bfs_server_submit(h, gid, int(sources[gid][si]), d, p, t0 + off)
+            outstanding[t] = (gid, d, p)
+            i += 1
+        for rec in bfs.bfs_server_poll(h, 256, 0 if i < len(trace) else 5):
+            gid, d, p = outstanding.pop(rec.ticket)
+            pools[gid].append((d, p))
+            lat.append(rec.t_done_ns - rec.t_arrival_ns)
+            bad += rec.status != 0
+            t_last = max(t_last, rec.t_done_ns)
+    out = latency_summary(lat, t0, t_last, len(trace))
+    out["failed"] = bad
+    return out
+
+
+def one_at_a_time(graphs, sources, trace, stream):
+    """The same arrivals served FIFO, one bfs_run (single-source kernel, whole
+    device) per query, each checked for its device status before the next."""
+    import torch
+
+    import paper_1803_03922_gb300 as bfs
+
+    outs = [(torch.empty(g.n, dtype=torch.int32, device="cuda"),
+             torch.empty(g.n, dtype=torch.int32, device="cuda")) for g in graphs]
+    t0 = bfs.bfs_server_now_ns() + 2_000_000
+    lat = []
+    for off, gid, si in trace:
+        ta = t0 + off
+        while bfs.bfs_server_now_ns() < ta:
+            pass
+        g = graphs[gid]
+        g.run(int(sources[gid][si]), outs[gid][0], outs[gid][1], stream=stream)
+        g.wait(stream)
+        lat.append(bfs.bfs_server_now_ns() - ta)
+    t_last = t0 + trace[-1][0] + lat[-1]
+    return latency_summary(lat, t0, t_last, len(trace))
+
+
+def serving_bench(stream, rates=SERVE_RATES, duration_s=1.5, single_cap=2000, max_concurrent=2):
+    """Serving loop over five device-resident graphs (RMAT scales 18/20/22/24 and
+    Erdos-Renyi 2^22 with average degree 16): Poisson arrivals at each rate, uniform
+    over graphs and over each graph's non-isolated sources; the server against the
+    same arrivals served one at a time.  Also a saturation run (every query
+    arrives at once): the server's peak queries/s."""
+    import torch
+
+    import paper_1803_03922_gb300 as bfs
+
+    graphs, sources = [], []
+    for name, w in SERVE_GRAPHS:
+        g, s = build_served_graph(w)
+        graphs.append(g)
+        sources.append(s)
+    srv = bfs.Server(max_concurrent=max_concurrent, max_lanes=64, with_parents=True)
+    for g in graphs:
+        srv.add_graph(g)
+    pools = [[(torch.empty(g.n, dtype=torch.uint8, device="cuda"), torch.empty(g.n, dtype=torch.int32, device="cuda"))
+              for _ in range(SERVE_POOL)] for g in graphs]
+    out = {"graphs": [name for name, _ in SERVE_GRAPHS], "max_concurrent": max_concurrent,
+           "pool_per_graph": SERVE_POOL, "one_at_a_time_queries": single_cap, "rates": {}}
+    # warm-up: every graph's contexts
+    serve_open_loop(srv, graphs, sources, pools, serve_trace(20000, 400, len(graphs), SERVE_SOURCES, 1))
+    for rate in rates:
+        trace = serve_trace(rate, max(200, int(rate * duration_s)), len(graphs), SERVE_SOURCES, rate)
+        r = {"server": serve_open_loop(srv, graphs, sources, pools, trace)}
+        r["one_at_a_time"] = one_at_a_time(graphs, sources, trace[:single_cap], stream)
+        out["rates"][str(rate)] = r
+    sat = serve_trace(1e9, 4000, len(graphs), SERVE_SOURCES, 99)
+    out["saturation_server"] = serve_open_loop(srv, graphs, sources, pools, sat)
+    out["saturation_one_at_a_time"] = one_at_a_time(graphs, sources, sat[:single_cap], stream)
+    out["server_stats"] = srv.stats()
+    srv.close()
+    del pools
+    for g in graphs:
+        g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_extras(stream):
+    out = {}
+    try:
+        g, srcs = build_served_graph(WORKLOADS["rmat24"])
+        out["batched_rmat24"] = batched_vs_single(g, srcs)
+        g.close()
+    except Exception as e:  # report, do not hide
+        out["batched_rmat24"] = {"error": str(e)}
+    try:
+        out["serving"] = serving_bench(stream)
+    except Exception as e:
+        out["serving"] = {"error": str(e)}
+    return out
+
+
 def config_of(name, w, info=None):
     c = {"workload": name, "graph": "RMAT" if w["kind"] == "rmat" else "Erdos-Renyi", "scale": w["scale"],
          "n": 1 << w["scale"], "th": w["th"], "alpha": 15, "beta": 18, "sources": N_SOURCES,
@@ -377,6 +585,8 @@ def main():
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the TH sweep and the scale-26 graphs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serving-only", action="store_true", help="print only the batched and serving measurements")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     w = WORKLOADS[args.workload]
@@ -387,6 +597,9 @@ def main():
     import torch
 
     torch.cuda.set_device(local)
+    if args.serving_only:
+        print(json.dumps(serving_extras(torch.cuda.current_stream())), flush=True)
+        return
     if ws > 1:
         import torch.distributed as dist
 
@@ -490,6 +703,8 @@ def main():
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not hide
                 extras[name] = {"error": str(e)}
+        if not args.no_serving:
+            extras.update(serving_extras(stream))
         line["extras"] = extras
 
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -190,9 +190,18 @@ typedef struct bfs_batch_stats {
 } bfs_batch_stats;
 
 /* Device state for batches on graph g (about 8*4 + 64 (+256 with parents) bytes per
- * non-isolated vertex).  One batch at a time per context; several contexts on
- * different streams may run concurrently.  The graph must outlive the context. */
-int bfs_batch_create(const bfs_graph* g, int32_t with_parents, bfs_batch** out);
+ * non-isolated vertex).  ctas: CTAs of the context's cooperative launch (0 = two
+ * per SM, the whole device).  One batch at a time per context; contexts on
+ * different streams may run concurrently only if their ctas add up to at most
+ * the device's co-resident capacity (bfs_batch_capacity), so that every launch
+ * can be resident at once.  The graph must outlive the context. */
+int bfs_batch_create(const bfs_graph* g, int32_t with_parents, int32_t ctas, bfs_batch** out);
+
+/* Co-resident CTA capacity of the batched kernel on the current device (two per SM). */
+int bfs_batch_capacity(int32_t* ctas);
+
+/* Device bytes held by a batch context. */
+int64_t bfs_batch_device_bytes(const bfs_batch* b);
 
 /* k (1..64) queries from sources[0..k) (host array of caller ids; repeats allowed).
  * depth[k*n] uint8 row-major by query (255 = unreached); parent[k*n] int32 (may be
@@ -206,6 +215,92 @@ int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, uint8_t* dept
 int bfs_batch_wait(bfs_batch* b, struct CUstream_st* stream);
 
 void bfs_batch_free(bfs_batch* b);
+
+/* ---- Serving loop: continuous batching of queries over device-resident graphs. ----
+ * Not in the paper, which runs one source at a time.  A server borrows graph
+ * handles and owns a worker thread.  Submitted queries wait in one FIFO per
+ * graph.  Whenever fewer than max_concurrent launches are in flight, the worker
+ * takes the graph whose oldest waiting query arrived first, packs up to
+ * max_lanes of that graph's waiting queries into one multi-source launch (the
+ * kernel of bfs_run_batch, so each query gets exactly the result bfs_run_batch
+ * gives it alone) on a stream of its own, and reports each query when its
+ * launch ends.  Each launch gets capacity / max_concurrent CTAs, so all launches
+ * in flight are co-resident.  Batch contexts are created on demand (at most
+ * contexts_per_graph per graph); a new context is admitted only when the
+ * device's free memory less hbm_reserve_bytes covers it and the bytes of all
+ * contexts held stay within hbm_budget_bytes; otherwise idle contexts of other
+ * graphs are freed, least recently used first, or the queries keep waiting.
+ * The submitting thread, the worker and the polling thread may differ. */
+typedef struct bfs_server bfs_server;
+
+typedef struct bfs_server_options {
+  int32_t max_concurrent;     /* launches in flight, 1..8 (0 = 2) */
+  int32_t max_lanes;          /* queries per launch, 1..64 (0 = 64) */
+  int32_t with_parents;       /* 1: every query writes parents as well as depths */
+  int32_t contexts_per_graph; /* batch contexts per graph, 1..max_concurrent (0 = max_concurrent) */
+  int64_t hbm_reserve_bytes;  /* device memory left free when a context is admitted */
+  int64_t hbm_budget_bytes;   /* cap on the device bytes of all contexts held (0 = none) */
+  int32_t reserved[8];        /* zero */
+} bfs_server_options;
+
+typedef struct bfs_server_done {
+  int64_t ticket;       /* as returned by bfs_server_submit */
+  int32_t status;       /* BFS_OK, or the negative code of its launch (TIMEOUT, OVERFLOW, CUDA) */
+  int32_t graph_id;
+  int32_t batch_size;   /* queries in its launch */
+  int32_t levels;       /* levels of its launch */
+  int64_t t_arrival_ns; /* bfs_server_now_ns() clock throughout */
+  int64_t t_launch_ns;
+  int64_t t_done_ns;
+  int64_t device_ns;    /* %globaltimer span of its launch */
+} bfs_server_done;
+
+typedef struct bfs_server_stats {
+  int64_t submitted, completed, failed;
+  int64_t launches, lanes_launched;
+  int64_t contexts_created, contexts_evicted;
+  int64_t context_bytes;  /* device bytes of the contexts held now */
+  int64_t waiting;        /* queries submitted and not launched */
+  int64_t in_flight;      /* launches running */
+  int32_t capacity_ctas;  /* co-resident CTAs of the batched kernel on the device */
+  int32_t ctas_per_launch;
+  int64_t reserved[4];
+} bfs_server_stats;
+
+void bfs_server_options_default(bfs_server_options* opt);
+
+/* Creates a server on the current device.  Errors: INVALID (option out of range), CUDA, OOM. */
+int bfs_server_create(const bfs_server_options* opt, bfs_server** out);
+
+/* Registers a graph (borrowed: it must outlive the server and must not run
+ * bfs_run concurrently with the server's launches).  *graph_id = 0, 1, ... */
+int bfs_server_add_graph(bfs_server* s, const bfs_graph* g, int32_t* graph_id);
+
+/* Host monotonic clock in ns (the clock of every bfs_server_done time). */
+int64_t bfs_server_now_ns(void);
+
+/* Queues a query from `source` (caller id) on graph graph_id.  depth[n] uint8
+ * (255 = unreached) and, for a server with parents, parent[n] int32 (NULL
+ * otherwise): caller-owned DEVICE buffers that must stay valid until the query
+ * is reported.  t_arrival_ns: the query's arrival on bfs_server_now_ns()'s clock,
+ * the start of its latency (0 = now).  *ticket: 1, 2, ... in submission order.
+ * Errors: INVALID (bad graph id, source, buffer or a destroyed server). */
+int bfs_server_submit(bfs_server* s, int32_t graph_id, int32_t source, uint8_t* depth, int32_t* parent,
+                      int64_t t_arrival_ns, int64_t* ticket);
+
+/* Moves up to max_done finished queries into done[] (host array), oldest
+ * completion first; waits up to timeout_ms (0 = do not wait, < 0 = until one is
+ * done or nothing is queued or running) for the first.  *n_done = the count. */
+int bfs_server_poll(bfs_server* s, bfs_server_done* done, int32_t max_done, int32_t timeout_ms, int32_t* n_done);
+
+int bfs_server_get_stats(bfs_server* s, bfs_server_stats* st);
+
+/* Waits for the launches in flight, reports nothing more, frees every context
+ * and stops the worker; queries not yet launched are dropped.  NULL is a no-op. */
+void bfs_server_destroy(bfs_server* s);
+
+/* sizeof of bfs_server_options, bfs_server_done, bfs_server_stats. */
+void bfs_server_abi_sizes(int64_t sizes[3]);
 
 /* Synchronizes `stream` and returns the device-side status of the graph's most
  * recent run: BFS_OK, or BFS_ERR_TIMEOUT when a bounded wait expired (runs with

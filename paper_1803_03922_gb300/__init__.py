@@ -84,6 +84,25 @@ class bfs_batch_stats(ctypes.Structure):
                 ("level", bfs_batch_level * BFS_BATCH_LOG_LEVELS)]
 
 
+class bfs_server_options(ctypes.Structure):
+    _fields_ = [("max_concurrent", c_i32), ("max_lanes", c_i32), ("with_parents", c_i32),
+                ("contexts_per_graph", c_i32), ("hbm_reserve_bytes", c_i64), ("hbm_budget_bytes", c_i64),
+                ("reserved", c_i32 * 8)]
+
+
+class bfs_server_done(ctypes.Structure):
+    _fields_ = [("ticket", c_i64), ("status", c_i32), ("graph_id", c_i32), ("batch_size", c_i32),
+                ("levels", c_i32), ("t_arrival_ns", c_i64), ("t_launch_ns", c_i64), ("t_done_ns", c_i64),
+                ("device_ns", c_i64)]
+
+
+class bfs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_i64), ("completed", c_i64), ("failed", c_i64), ("launches", c_i64),
+                ("lanes_launched", c_i64), ("contexts_created", c_i64), ("contexts_evicted", c_i64),
+                ("context_bytes", c_i64), ("waiting", c_i64), ("in_flight", c_i64),
+                ("capacity_ctas", c_i32), ("ctas_per_launch", c_i32), ("reserved", c_i64 * 4)]
+
+
 class BfsError(RuntimeError):
     def __init__(self, code, message):
         super().__init__("bfs error %d: %s" % (code, message))
@@ -115,11 +134,32 @@ def _load():
     lib.bfs_free.restype = None
     lib.bfs_last_error.restype = ctypes.c_char_p
     lib.bfs_last_error.argtypes = []
-    lib.bfs_batch_create.argtypes = [c_vp, c_i32, ctypes.POINTER(c_vp)]
+    lib.bfs_batch_create.argtypes = [c_vp, c_i32, c_i32, ctypes.POINTER(c_vp)]
+    lib.bfs_batch_capacity.argtypes = [ctypes.POINTER(c_i32)]
+    lib.bfs_batch_device_bytes.argtypes = [c_vp]
+    lib.bfs_batch_device_bytes.restype = c_i64
     lib.bfs_run_batch.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(bfs_batch_stats), c_vp]
     lib.bfs_batch_wait.argtypes = [c_vp, c_vp]
     lib.bfs_batch_free.argtypes = [c_vp]
     lib.bfs_batch_free.restype = None
+    lib.bfs_server_options_default.argtypes = [ctypes.POINTER(bfs_server_options)]
+    lib.bfs_server_options_default.restype = None
+    lib.bfs_server_create.argtypes = [ctypes.POINTER(bfs_server_options), ctypes.POINTER(c_vp)]
+    lib.bfs_server_add_graph.argtypes = [c_vp, c_vp, ctypes.POINTER(c_i32)]
+    lib.bfs_server_now_ns.argtypes = []
+    lib.bfs_server_now_ns.restype = c_i64
+    lib.bfs_server_submit.argtypes = [c_vp, c_i32, c_i32, c_vp, c_vp, c_i64, ctypes.POINTER(c_i64)]
+    lib.bfs_server_poll.argtypes = [c_vp, ctypes.POINTER(bfs_server_done), c_i32, c_i32, ctypes.POINTER(c_i32)]
+    lib.bfs_server_get_stats.argtypes = [c_vp, ctypes.POINTER(bfs_server_stats)]
+    lib.bfs_server_destroy.argtypes = [c_vp]
+    lib.bfs_server_destroy.restype = None
+    lib.bfs_server_abi_sizes.argtypes = [ctypes.POINTER(c_i64 * 3)]
+    lib.bfs_server_abi_sizes.restype = None
+    ssz = (c_i64 * 3)()
+    lib.bfs_server_abi_sizes(ctypes.byref(ssz))
+    swant = [ctypes.sizeof(t) for t in (bfs_server_options, bfs_server_done, bfs_server_stats)]
+    if list(ssz) != swant:
+        raise ImportError("server ABI struct sizes differ: library %s, binding %s" % (list(ssz), swant))
     lib.bfs_abi_sizes.argtypes = [ctypes.POINTER(c_i64 * 5)]
     lib.bfs_abi_sizes.restype = None
     sizes = (c_i64 * 5)()
@@ -237,10 +277,20 @@ def bfs_run_static(row_off, col, n: int, source: int, depth, parent, stream=None
                                   _stream(stream)))
 
 
-def bfs_batch_create(g, with_parents: bool = True):
+def bfs_batch_create(g, with_parents: bool = True, ctas: int = 0):
     h = c_vp()
-    _check(_load().bfs_batch_create(g, 1 if with_parents else 0, ctypes.byref(h)))
+    _check(_load().bfs_batch_create(g, 1 if with_parents else 0, int(ctas), ctypes.byref(h)))
     return h
+
+
+def bfs_batch_capacity() -> int:
+    c = c_i32()
+    _check(_load().bfs_batch_capacity(ctypes.byref(c)))
+    return int(c.value)
+
+
+def bfs_batch_device_bytes(b) -> int:
+    return int(_load().bfs_batch_device_bytes(b))
 
 
 def bfs_run_batch(b, sources, depth, parent=None, stats: bfs_batch_stats | None = None, stream=None):
@@ -258,6 +308,53 @@ def bfs_batch_wait(b, stream=None):
 def bfs_batch_free(b):
     if b:
         _load().bfs_batch_free(b)
+
+
+def bfs_server_options_default() -> bfs_server_options:
+    o = bfs_server_options()
+    _load().bfs_server_options_default(ctypes.byref(o))
+    return o
+
+
+def bfs_server_create(opt: bfs_server_options | None = None):
+    h = c_vp()
+    _check(_load().bfs_server_create(ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
+    return h
+
+
+def bfs_server_add_graph(s, g) -> int:
+    gid = c_i32()
+    _check(_load().bfs_server_add_graph(s, g, ctypes.byref(gid)))
+    return int(gid.value)
+
+
+def bfs_server_now_ns() -> int:
+    return int(_load().bfs_server_now_ns())
+
+
+def bfs_server_submit(s, graph_id: int, source: int, depth, parent=None, t_arrival_ns: int = 0) -> int:
+    t = c_i64()
+    _check(_load().bfs_server_submit(s, int(graph_id), int(source), _ptr(depth), _ptr(parent),
+                                     int(t_arrival_ns), ctypes.byref(t)))
+    return int(t.value)
+
+
+def bfs_server_poll(s, max_done: int = 256, timeout_ms: int = 0):
+    buf = (bfs_server_done * max_done)()
+    n = c_i32()
+    _check(_load().bfs_server_poll(s, buf, int(max_done), int(timeout_ms), ctypes.byref(n)))
+    return [buf[i] for i in range(n.value)]
+
+
+def bfs_server_get_stats(s) -> bfs_server_stats:
+    st = bfs_server_stats()
+    _check(_load().bfs_server_get_stats(s, ctypes.byref(st)))
+    return st
+
+
+def bfs_server_destroy(s):
+    if s:
+        _load().bfs_server_destroy(s)
 
 
 def bfs_free(g):
@@ -326,10 +423,11 @@ class Graph:
 class Batch:
     """Device state for 64-lane batches of queries on a Graph."""
 
-    def __init__(self, graph: "Graph", with_parents: bool = True):
+    def __init__(self, graph: "Graph", with_parents: bool = True, ctas: int = 0):
         self.graph = graph
         self.with_parents = with_parents
-        self._h = bfs_batch_create(graph.handle, with_parents)
+        self._h = bfs_batch_create(graph.handle, with_parents, ctas)
+        self.device_bytes = bfs_batch_device_bytes(self._h)
 
     def run(self, sources, depth=None, parent=None, stats: bool = False, stream=None):
         """Runs len(sources) <= 64 queries; returns (depth [k, n] uint8, parent [k, n] int32 or
@@ -353,6 +451,86 @@ class Batch:
         if getattr(self, "_h", None):
             bfs_batch_free(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching query server over device-resident Graphs (bfs_server_*)."""
+
+    def __init__(self, max_concurrent: int = 2, max_lanes: int = 64, with_parents: bool = True,
+                 contexts_per_graph: int = 0, hbm_reserve_bytes: int = 0, hbm_budget_bytes: int = 0):
+        o = bfs_server_options_default()
+        o.max_concurrent = max_concurrent
+        o.max_lanes = max_lanes
+        o.with_parents = 1 if with_parents else 0
+        o.contexts_per_graph = contexts_per_graph
+        o.hbm_reserve_bytes = hbm_reserve_bytes
+        o.hbm_budget_bytes = hbm_budget_bytes
+        self.with_parents = with_parents
+        self.graphs = []
+        self._live = {}  # ticket -> (depth, parent) kept alive until reported
+        self._h = bfs_server_create(o)
+
+    def add_graph(self, graph: "Graph") -> int:
+        gid = bfs_server_add_graph(self._h, graph.handle)
+        self.graphs.append(graph)
+        return gid
+
+    @staticmethod
+    def now_ns() -> int:
+        return bfs_server_now_ns()
+
+    def submit(self, graph_id: int, source: int, depth=None, parent=None, t_arrival_ns: int = 0) -> int:
+        """Queues one query; depth (uint8 [n]) and parent (int32 [n]) are CUDA tensors
+        (allocated when not given) that the poll record hands back."""
+        import torch
+
+        n = self.graphs[graph_id].n
+        if depth is None:
+            depth = torch.empty(n, dtype=torch.uint8, device="cuda")
+        if parent is None and self.with_parents:
+            parent = torch.empty(n, dtype=torch.int32, device="cuda")
+        t = bfs_server_submit(self._h, graph_id, source, depth, parent if self.with_parents else None,
+                              t_arrival_ns)
+        self._live[t] = (depth, parent)
+        return t
+
+    def poll(self, timeout_ms: int = 0, max_done: int = 256):
+        """Finished queries as dicts (ticket, status, graph_id, batch_size, levels, times,
+        depth, parent)."""
+        out = []
+        for d in bfs_server_poll(self._h, max_done, timeout_ms):
+            rec = {f: getattr(d, f) for f, _ in bfs_server_done._fields_}
+            rec["depth"], rec["parent"] = self._live.pop(d.ticket, (None, None))
+            out.append(rec)
+        return out
+
+    def drain(self, timeout_s: float = 120.0):
+        """Polls until every submitted query is reported."""
+        import time
+
+        out = []
+        t_end = time.monotonic() + timeout_s
+        while self._live:
+            if time.monotonic() > t_end:
+                raise TimeoutError("%d queries still outstanding" % len(self._live))
+            out += self.poll(timeout_ms=100)
+        return out
+
+    def stats(self) -> dict:
+        st = bfs_server_get_stats(self._h)
+        return {f: getattr(st, f) for f, _ in bfs_server_stats._fields_ if f != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            bfs_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
 
     def __del__(self):
         try:

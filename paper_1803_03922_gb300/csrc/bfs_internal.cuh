@@ -145,4 +145,14 @@ int cuda_fail(cudaError_t e, const char* what);
 int configure_run(bfs_graph* g);
 int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s);
 int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st);
+
+// Multi-source batches (msbfs.cu).  ms_batch_bytes: device bytes of a batch
+// context.  ms_launch: one asynchronous launch on s with per-lane output rows
+// (parent == nullptr: depths only), then a copy of the run header to hdr_out
+// (pinned host, may be null); *epoch_out gets the run's epoch for
+// ms_header_status, which turns a header into BFS_OK or the run's error code.
+int64_t ms_batch_bytes(const bfs_graph* g, int with_parents);
+int ms_header_status(const RunHeader& h, unsigned epoch);
+int ms_launch(bfs_batch* b, const int32_t* sources, int k, uint8_t* const* depth, int32_t* const* parent,
+              cudaStream_t s, RunHeader* hdr_out, unsigned* epoch_out);
 }  // namespace bfsgb

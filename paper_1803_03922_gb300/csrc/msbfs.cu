@@ -53,23 +53,25 @@ struct MsParams {
   unsigned long long* F0;
   unsigned long long* F1;
   unsigned long long* F2;
-  uint8_t* depth_i;   // [n_ni][64] (vertex-major: a vertex's lanes share cache lines)
-  int32_t* parent_i;  // [n_ni][64] or null
+  uint8_t* depth_i;   // [n_ni][ls] (vertex-major: a vertex's lanes share cache lines)
+  int32_t* parent_i;  // [n_ni][ls] or null
   int2* CL0;
   int2* CL1;
   MsSlot* slot;       // [4]
   MsLog* log;         // [BFS_BATCH_LOG_LEVELS]
   RunHeader* hdr;
   unsigned long long* arrive;
-  uint8_t* out_depth;   // [k][n]
-  int32_t* out_parent;  // [k][n] or null
   int64_t nnz;
   int32_t n, n_ni, d, k;
+  int32_t ls;           // lane stride of depth_i / parent_i: k rounded up to a multiple of 4
+  int32_t out_parents;  // 1: out_p[j] are written
   int32_t alpha;
   unsigned int epoch;
   unsigned long long timeout_ns;
   unsigned long long run_timeout_ns;
   int32_t src_c[kMsLanes];
+  uint8_t* out_d[kMsLanes];  // lane j's depth row, n entries in caller ids
+  int32_t* out_p[kMsLanes];  // lane j's parent row (when out_parents)
 };
 
 __device__ __forceinline__ unsigned long long* Fbuf(const MsParams& p, int i) {
@@ -81,7 +83,7 @@ __device__ __forceinline__ void ms_offer(const MsParams& p, int v, unsigned long
   while (nb) {
     const int b = __ffsll((long long)nb) - 1;
     nb &= nb - 1;
-    atomicMin(p.parent_i + (int64_t)v * kMsLanes + b, pc);
+    atomicMin(p.parent_i + (int64_t)v * p.ls + b, pc);
   }
 }
 
@@ -166,8 +168,8 @@ __device__ __forceinline__ void ms_found(const MsParams& p, int v, unsigned long
   while (nb) {
     const int b = __ffsll((long long)nb) - 1;
     nb &= nb - 1;
-    if (p.parent_i) p.parent_i[(int64_t)v * kMsLanes + b] = -(u + 1);
-    p.depth_i[(int64_t)v * kMsLanes + b] = (uint8_t)(L + 1);
+    if (p.parent_i) p.parent_i[(int64_t)v * p.ls + b] = -(u + 1);
+    p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
   }
 }
 
@@ -288,7 +290,7 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
           while (x) {
             const int b = __ffsll((long long)x) - 1;
             x &= x - 1;
-            p.depth_i[(int64_t)v * kMsLanes + b] = (uint8_t)(L + 1);
+            p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
           }
         }
         if (v < p.d) nch = ((unsigned long long)dg + kChunk - 1) / kChunk;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     p.F2[v] = 0ull;
   }
   if (p.parent_i) {
-    const int64_t P4 = (int64_t)p.n_ni * (kMsLanes / 4);
+    const int64_t P4 = (int64_t)p.n_ni * (p.ls / 4);
     for (int64_t i = gtid; i < P4; i += gthreads)
       reinterpret_cast<int4*>(p.parent_i)[i] = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
   }
@@ -362,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
       }
       p.F0[v] |= bit;
       p.visit[v] |= bit;
-      p.depth_i[(int64_t)v * kMsLanes + j] = 0;
-      if (p.parent_i) p.parent_i[(int64_t)v * kMsLanes + j] = p.src_c[j];
+      p.depth_i[(int64_t)v * p.ls + j] = 0;
+      if (p.parent_i) p.parent_i[(int64_t)v * p.ls + j] = p.src_c[j];
       pdeg += (unsigned long long)dg;
     }
     p.slot[0].nfv = nfv;
@@ -418,8 +420,8 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     if (bits < 0) return;
     ++L;
   }
-  // results in caller ids: out[j][c] for the k lanes, a vertex's lanes read four
-  // at a time (its 64 depth bytes and 64 parents are contiguous)
+  // results in caller ids: out_d[j][c] for the k lanes, a vertex's lanes read
+  // four at a time (its depth bytes and parents are contiguous)
   if (leader) p.hdr->t_loop = gtimer();
   for (int64_t c = gtid; c < p.n; c += gthreads) {
     const int v = p.internal_of[c];
@@ -429,8 +431,8 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
       unsigned dq = 0xFFFFFFFFu;
       int4 pq = make_int4(-1, -1, -1, -1);
       if (in && ((vis >> j0) & 0xFull)) {
-        dq = *reinterpret_cast<const unsigned*>(p.depth_i + (int64_t)v * kMsLanes + j0);
-        if (p.parent_i && p.out_parent) pq = *reinterpret_cast<const int4*>(p.parent_i + (int64_t)v * kMsLanes + j0);
+        dq = *reinterpret_cast<const unsigned*>(p.depth_i + (int64_t)v * p.ls + j0);
+        if (p.out_parents) pq = *reinterpret_cast<const int4*>(p.parent_i + (int64_t)v * p.ls + j0);
       }
       const int pv4[4] = {pq.x, pq.y, pq.z, pq.w};
 #pragma unroll
@@ -445,13 +447,13 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
           dv = 0;
           pv = p.src_c[j];
         }
-        p.out_depth[(int64_t)j * p.n + c] = dv;
-        if (p.out_parent) p.out_parent[(int64_t)j * p.n + c] = pv;
+        p.out_d[j][c] = dv;
+        if (p.out_parents) p.out_p[j][c] = pv;
       }
     }
   }
-  if (leader) {
-    p.hdr->levels = L;
+  if (leader) {  // every query reaches its source: max depth + 1 >= 1 even if all sources are isolated
+    p.hdr->levels = L > 0 ? L : 1;
     p.hdr->levels_run = L;
     p.hdr->t1 = gtimer();
     p.hdr->reached = s_pairs;
@@ -513,8 +515,22 @@ bool dev_ptr(const void* q) {
 
 }  // namespace
 
-extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, bfs_batch** out) {
+extern "C" int bfs_batch_capacity(int32_t* ctas) {
+  if (!ctas) return fail(BFS_ERR_INVALID, "ctas is NULL");
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_loop, kThreads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs_batch_capacity");
+  *ctas = sms * (per_sm < 2 ? per_sm : 2);
+  return BFS_OK;
+}
+
+extern "C" int64_t bfs_batch_device_bytes(const bfs_batch* b) { return b ? b->device_bytes : 0; }
+
+extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, int32_t ctas, bfs_batch** out) {
   if (!g || !out) return fail(BFS_ERR_INVALID, "graph or out is NULL");
+  if (ctas < 0) return fail(BFS_ERR_INVALID, "ctas must be >= 0");
   *out = nullptr;
   bfs_batch* b = new (std::nothrow) bfs_batch();
   if (!b) return fail(BFS_ERR_OOM, "host allocation failed");
@@ -545,7 +561,11 @@ extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, bfs_ba
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_loop, kThreads, 0);
     if (e != cudaSuccess) rc = cuda_fail(e, "occupancy");
     else if (per_sm < 1) rc = fail(BFS_ERR_CUDA, "multi-source kernel does not fit on an SM");
-    else b->grid = sms * (per_sm < 2 ? per_sm : 2);
+    else {
+      const int cap = sms * (per_sm < 2 ? per_sm : 2);
+      if (ctas > cap) rc = fail(BFS_ERR_INVALID, "ctas exceeds the co-resident capacity");
+      b->grid = ctas > 0 ? ctas : cap;
+    }
   }
   if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
   if (rc) {
@@ -558,6 +578,80 @@ extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, bfs_ba
   *out = b;
   return BFS_OK;
 }
+
+namespace bfsgb {
+
+int64_t ms_batch_bytes(const bfs_graph* g, int with_parents) {
+  const int64_t nn = (int64_t)g->n_ni + 1;
+  return nn * 8 * 4 + (int64_t)kMsLanes * nn * (with_parents ? 5 : 1) + 2 * (int64_t)g->cl_cap * 8 +
+         4 * (int64_t)sizeof(MsSlot) + BFS_BATCH_LOG_LEVELS * (int64_t)sizeof(MsLog) + (int64_t)sizeof(RunHeader) +
+         (int64_t)kMaxBlocks * 32;
+}
+
+int ms_header_status(const RunHeader& h, unsigned epoch) {
+  if (h.err != 0 && (h.err >> 4) == (epoch & 0x0FFFFFFFu)) {
+    const int code = -(int)(h.err & 0xFu);
+    return fail(code, code == BFS_ERR_OVERFLOW ? "a depth exceeds 254 (uint8 depth of the batched form)"
+                                               : "a device-side wait of the multi-source loop passed its deadline");
+  }
+  return BFS_OK;
+}
+
+int ms_launch(bfs_batch* b, const int32_t* sources, int k, uint8_t* const* depth, int32_t* const* parent,
+              cudaStream_t s, RunHeader* hdr_out, unsigned* epoch_out) {
+  const bfs_graph* g = b->g;
+  MsParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.off = g->off;
+  p.col = g->col;
+  p.deg = g->deg;
+  p.caller_of = g->caller_of;
+  p.internal_of = g->internal_of;
+  const size_t nn = (size_t)g->n_ni + 1;
+  p.visit = b->visit;
+  p.F0 = b->F;
+  p.F1 = b->F + nn;
+  p.F2 = b->F + 2 * nn;
+  p.depth_i = b->depth_i;
+  p.parent_i = parent ? b->parent_i : nullptr;
+  p.CL0 = b->CL;
+  p.CL1 = b->CL + g->cl_cap;
+  p.slot = b->slot;
+  p.log = b->log;
+  p.hdr = b->hdr;
+  p.arrive = b->arrive;
+  p.nnz = g->nnz;
+  p.n = g->n;
+  p.n_ni = g->n_ni;
+  p.d = g->d;
+  p.k = k;
+  p.ls = (k + 3) & ~3;
+  p.out_parents = parent ? 1 : 0;
+  p.alpha = g->opt.alpha;
+  p.timeout_ns = (unsigned long long)g->opt.barrier_timeout_ms * 1000000ull;
+  p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
+  for (int j = 0; j < k; ++j) {
+    p.src_c[j] = sources[j];
+    p.out_d[j] = depth[j];
+    p.out_p[j] = parent ? parent[j] : nullptr;
+  }
+  p.epoch = ++b->epoch & 0x0FFFFFFFu;
+  if (p.epoch == 0) p.epoch = ++b->epoch & 0x0FFFFFFFu;
+  cudaError_t e = cudaSuccess;
+  if (p.epoch == 1) {
+    e = cudaMemsetAsync(b->arrive, 0, (size_t)kMaxBlocks * 4 * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&b->hdr->release, 0, 8, s);
+  }
+  void* args[] = {&p};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void*)ms_bfs_loop, dim3(b->grid), dim3(kThreads), args, 0, s);
+  if (e == cudaSuccess && hdr_out) e = cudaMemcpyAsync(hdr_out, b->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "multi-source launch");
+  if (epoch_out) *epoch_out = p.epoch;
+  return BFS_OK;
+}
+
+}  // namespace bfsgb
 
 extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, uint8_t* depth, int32_t* parent,
                              bfs_batch_stats* stats, struct CUstream_st* stream) {
@@ -586,65 +680,31 @@ extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, ui
     od = b->out_depth;
     op = parent ? b->out_parent : nullptr;
   }
+  unsigned epoch = 0;
   if (!rc) {
-    MsParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.off = g->off;
-    p.col = g->col;
-    p.deg = g->deg;
-    p.caller_of = g->caller_of;
-    p.internal_of = g->internal_of;
-    const size_t nn = (size_t)g->n_ni + 1;
-    p.visit = b->visit;
-    p.F0 = b->F;
-    p.F1 = b->F + nn;
-    p.F2 = b->F + 2 * nn;
-    p.depth_i = b->depth_i;
-    p.parent_i = parent ? b->parent_i : nullptr;
-    p.CL0 = b->CL;
-    p.CL1 = b->CL + g->cl_cap;
-    p.slot = b->slot;
-    p.log = b->log;
-    p.hdr = b->hdr;
-    p.arrive = b->arrive;
-    p.out_depth = od;
-    p.out_parent = op;
-    p.nnz = g->nnz;
-    p.n = g->n;
-    p.n_ni = g->n_ni;
-    p.d = g->d;
-    p.k = k;
-    p.alpha = g->opt.alpha;
-    p.timeout_ns = (unsigned long long)g->opt.barrier_timeout_ms * 1000000ull;
-    p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
-    for (int j = 0; j < k; ++j) p.src_c[j] = sources[j];
-    p.epoch = ++b->epoch & 0x0FFFFFFFu;
-    if (p.epoch == 0) p.epoch = ++b->epoch & 0x0FFFFFFFu;
-    cudaError_t e = cudaSuccess;
-    if (p.epoch == 1) {
-      e = cudaMemsetAsync(b->arrive, 0, (size_t)kMaxBlocks * 4 * 8, s);
-      if (e == cudaSuccess) e = cudaMemsetAsync(&b->hdr->release, 0, 8, s);
+    uint8_t* dl[kMsLanes];
+    int32_t* pl[kMsLanes];
+    for (int j = 0; j < k; ++j) {
+      dl[j] = od + (int64_t)j * g->n;
+      pl[j] = op ? op + (int64_t)j * g->n : nullptr;
     }
-    void* args[] = {&p};
-    if (e == cudaSuccess)
-      e = cudaLaunchCooperativeKernel((const void*)ms_bfs_loop, dim3(b->grid), dim3(kThreads), args, 0, s);
-    if (e == cudaSuccess && !dd) {
-      e = cudaMemcpyAsync(depth, od, (size_t)k * g->n, cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess && parent)
-        e = cudaMemcpyAsync(parent, op, (size_t)k * g->n * 4, cudaMemcpyDeviceToHost, s);
-    }
-    if (e != cudaSuccess) rc = cuda_fail(e, "multi-source launch");
-    if (!rc && (!dd || stats)) {
-      e = cudaStreamSynchronize(s);
-      RunHeader h;
-      if (e == cudaSuccess) e = cudaMemcpy(&h, b->hdr, sizeof(h), cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) {
-        rc = cuda_fail(e, "bfs_run_batch");
-      } else if (h.err != 0 && (h.err >> 4) == p.epoch) {
-        const int code = -(int)(h.err & 0xFu);
-        rc = fail(code, code == BFS_ERR_OVERFLOW ? "a depth exceeds 254 (uint8 depth of the batched form)"
-                                                 : "a device-side wait of the multi-source loop passed its deadline");
-      } else if (stats) {
+    rc = ms_launch(b, sources, k, dl, op ? pl : nullptr, s, nullptr, &epoch);
+  }
+  cudaError_t e = cudaSuccess;
+  if (!rc && !dd) {
+    e = cudaMemcpyAsync(depth, od, (size_t)k * g->n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent, op, (size_t)k * g->n * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy batch results");
+  }
+  if (!rc && (!dd || stats)) {
+    e = cudaStreamSynchronize(s);
+    RunHeader h;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, b->hdr, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "bfs_run_batch");
+    } else {
+      rc = ms_header_status(h, epoch);
+      if (!rc && stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->levels = h.levels;
         stats->pairs_reached = (int64_t)h.reached;
@@ -652,7 +712,7 @@ extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, ui
         stats->device_ns = h.t1 - h.t0;
         stats->setup_ns = h.t_init - h.t0;
         stats->result_ns = h.t1 - h.t_loop;
-        stats->logged_levels = h.levels < BFS_BATCH_LOG_LEVELS ? h.levels : BFS_BATCH_LOG_LEVELS;
+        stats->logged_levels = h.levels_run < BFS_BATCH_LOG_LEVELS ? h.levels_run : BFS_BATCH_LOG_LEVELS;
         MsLog lg[BFS_BATCH_LOG_LEVELS];
         if (stats->logged_levels > 0 &&
             cudaMemcpy(lg, b->log, sizeof(MsLog) * stats->logged_levels, cudaMemcpyDeviceToHost) == cudaSuccess) {
@@ -681,12 +741,7 @@ extern "C" int bfs_batch_wait(bfs_batch* b, struct CUstream_st* stream) {
   RunHeader h;
   e = cudaMemcpy(&h, b->hdr, sizeof(h), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read batch header");
-  if (h.err != 0 && (h.err >> 4) == (b->epoch & 0x0FFFFFFFu)) {
-    const int code = -(int)(h.err & 0xFu);
-    return fail(code, code == BFS_ERR_OVERFLOW ? "a depth exceeds 254 (uint8 depth of the batched form)"
-                                               : "a device-side wait of the multi-source loop passed its deadline");
-  }
-  return BFS_OK;
+  return ms_header_status(h, b->epoch);
 }
 
 extern "C" void bfs_batch_free(bfs_batch* b) {

@@ -1,0 +1,457 @@
+// Serving loop: continuous batching of BFS queries over device-resident graphs
+// (the bfs_server_* entry points).  The paper runs one source at a time; this is
+// the runtime that turns the 64-lane multi-source kernel into a query server.
+//
+// Threads: callers submit and poll under `mu`; one worker thread owns the batch
+// contexts and does every CUDA call of the server; a host function queued on a
+// context's stream after its launch stamps the completion time and wakes the
+// worker.  The worker never holds `mu` across a CUDA call (cudaFree and friends
+// wait for queued host functions, which take `mu`).
+//
+// Scheduling: one FIFO per graph.  While fewer than max_concurrent launches run,
+// the graph whose oldest waiting query arrived first gets an idle context (or a
+// new one, if free device memory and the budget admit it, after freeing idle
+// contexts of other graphs least recently used first) and one launch of up to
+// max_lanes of its waiting queries.  Every launch has capacity / max_concurrent
+// CTAs, so the cooperative launches in flight always fit on the device together.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "bfs_internal.cuh"
+
+using bfsgb::cuda_fail;
+using bfsgb::fail;
+using bfsgb::RunHeader;
+
+namespace {
+
+constexpr int kMaxLanes = 64;
+constexpr int kMaxConcurrent = 8;
+constexpr int64_t kStuckCheckNs = 1000000000;  // query a silent stream after 1 s
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Query {
+  int64_t ticket;
+  int32_t source;
+  uint8_t* depth;
+  int32_t* parent;
+  int64_t t_arrival;
+};
+
+struct GraphEntry {
+  const bfs_graph* g;
+  std::deque<Query> waiting;
+};
+
+struct Context {
+  bfs_server* srv = nullptr;
+  int gid = 0;
+  bfs_batch* b = nullptr;
+  cudaStream_t stream = nullptr;
+  RunHeader* hdr = nullptr;  // pinned host copy of the launch's run header
+  int64_t bytes = 0;
+  bool busy = false;
+  int64_t last_used = 0;
+  std::vector<Query> q;  // the queries of the launch in flight
+  unsigned epoch = 0;
+  int64_t t_launch = 0;
+  std::atomic<int64_t> t_done{0};  // stamped by the stream's host function; 0 while running
+};
+
+bool device_ptr(const void* q) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct bfs_server {
+  bfs_server_options opt{};
+  int device = 0;
+  int capacity = 0, slice = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  // guarded by mu
+  std::deque<GraphEntry> graphs;
+  std::deque<bfs_server_done> done;
+  int64_t next_ticket = 1;
+  int64_t waiting = 0;
+  int in_flight = 0;
+  bool stop = false, wake = false;
+  int64_t submitted = 0, completed = 0, failed = 0, launches = 0, lanes = 0;
+  int64_t created = 0, evicted = 0, ctx_bytes = 0;
+  // worker thread only
+  std::vector<std::unique_ptr<Context>> ctx;
+  std::thread worker;
+};
+
+namespace {
+
+void CUDART_CB on_launch_done(void* arg) {  // runs on a CUDA thread: no CUDA calls here
+  Context* c = static_cast<Context*>(arg);
+  c->t_done.store(now_ns(), std::memory_order_release);
+  bfs_server* s = c->srv;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->wake = true;
+  }
+  s->cv_work.notify_one();
+}
+
+// Moves the queries of a finished (or failed) launch to the done list.
+void finish(bfs_server* s, Context& c, int status, int64_t t_done) {
+  const int k = (int)c.q.size();
+  const int levels = status == BFS_OK ? c.hdr->levels : 0;
+  const int64_t dev = status == BFS_OK ? (int64_t)(c.hdr->t1 - c.hdr->t0) : 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (const Query& q : c.q) {
+      bfs_server_done d;
+      std::memset(&d, 0, sizeof(d));
+      d.ticket = q.ticket;
+      d.status = status;
+      d.graph_id = c.gid;
+      d.batch_size = k;
+      d.levels = levels;
+      d.t_arrival_ns = q.t_arrival;
+      d.t_launch_ns = c.t_launch;
+      d.t_done_ns = t_done;
+      d.device_ns = dev;
+      s->done.push_back(d);
+    }
+    s->completed += k;
+    if (status != BFS_OK) s->failed += k;
+    s->in_flight -= 1;
+  }
+  c.q.clear();
+  c.busy = false;
+  c.last_used = t_done;
+  s->cv_done.notify_all();
+}
+
+void reap(bfs_server* s) {
+  const int64_t now = now_ns();
+  for (auto& cp : s->ctx) {
+    Context& c = *cp;
+    if (!c.busy) continue;
+    const int64_t td = c.t_done.load(std::memory_order_acquire);
+    if (td) {
+      finish(s, c, bfsgb::ms_header_status(*c.hdr, c.epoch), td);
+    } else if (now - c.t_launch > kStuckCheckNs) {
+      // a stream whose work failed never runs its host function
+      const cudaError_t e = cudaStreamQuery(c.stream);
+      if (e != cudaSuccess && e != cudaErrorNotReady) finish(s, c, cuda_fail(e, "serving launch"), now_ns());
+    }
+  }
+}
+
+bool admit(bfs_server* s, int64_t bytes) {
+  int64_t held;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    held = s->ctx_bytes;
+  }
+  if (s->opt.hbm_budget_bytes > 0 && held + bytes > s->opt.hbm_budget_bytes) return false;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (int64_t)free_b >= bytes + s->opt.hbm_reserve_bytes;
+}
+
+void drop_context(bfs_server* s, size_t i) {
+  Context& c = *s->ctx[i];
+  bfs_batch_free(c.b);
+  if (c.stream) cudaStreamDestroy(c.stream);
+  if (c.hdr) cudaFreeHost(c.hdr);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ctx_bytes -= c.bytes;
+  }
+  s->ctx.erase(s->ctx.begin() + (std::ptrdiff_t)i);
+}
+
+// An idle context of graph gid, a new one, or null (the graph's queries wait).
+Context* acquire_context(bfs_server* s, int gid, const bfs_graph* g) {
+  int count = 0;
+  Context* idle = nullptr;
+  for (auto& cp : s->ctx)
+    if (cp->gid == gid) {
+      ++count;
+      if (!cp->busy && (!idle || cp->last_used > idle->last_used)) idle = cp.get();
+    }
+  if (idle) return idle;
+  if (count >= s->opt.contexts_per_graph) return nullptr;
+  const int64_t need = bfsgb::ms_batch_bytes(g, s->opt.with_parents);
+  while (!admit(s, need)) {
+    // free the least recently used idle context of another graph
+    size_t victim = s->ctx.size();
+    for (size_t i = 0; i < s->ctx.size(); ++i) {
+      const Context& c = *s->ctx[i];
+      if (c.busy || c.gid == gid) continue;
+      if (victim == s->ctx.size() || c.last_used < s->ctx[victim]->last_used) victim = i;
+    }
+    if (victim == s->ctx.size()) return nullptr;
+    drop_context(s, victim);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->evicted += 1;
+  }
+  std::unique_ptr<Context> c(new (std::nothrow) Context());
+  if (!c) return nullptr;
+  c->srv = s;
+  c->gid = gid;
+  if (bfs_batch_create(g, s->opt.with_parents, s->slice, &c->b) != BFS_OK) return nullptr;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hdr, sizeof(RunHeader)) != cudaSuccess) {
+    cudaGetLastError();
+    bfs_batch_free(c->b);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    return nullptr;
+  }
+  std::memset(c->hdr, 0, sizeof(RunHeader));
+  c->bytes = bfs_batch_device_bytes(c->b);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ctx_bytes += c->bytes;
+    s->created += 1;
+  }
+  s->ctx.push_back(std::move(c));
+  return s->ctx.back().get();
+}
+
+void launch(bfs_server* s, Context& c) {
+  const int k = (int)c.q.size();
+  int32_t src[kMaxLanes];
+  uint8_t* dl[kMaxLanes];
+  int32_t* pl[kMaxLanes];
+  for (int j = 0; j < k; ++j) {
+    src[j] = c.q[j].source;
+    dl[j] = c.q[j].depth;
+    pl[j] = c.q[j].parent;
+  }
+  c.busy = true;
+  c.t_done.store(0, std::memory_order_relaxed);
+  c.t_launch = now_ns();
+  int rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch);
+  if (rc == BFS_OK) {
+    const cudaError_t e = cudaLaunchHostFunc(c.stream, on_launch_done, &c);
+    if (e == cudaSuccess) return;
+    rc = cuda_fail(e, "queue completion callback");
+    cudaStreamSynchronize(c.stream);
+  }
+  finish(s, c, rc, now_ns());
+}
+
+void schedule(bfs_server* s) {
+  for (;;) {
+    std::vector<int> order;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (s->stop || s->in_flight >= s->opt.max_concurrent) return;
+      for (int i = 0; i < (int)s->graphs.size(); ++i)
+        if (!s->graphs[i].waiting.empty()) order.push_back(i);
+      std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const Query& qa = s->graphs[a].waiting.front();
+        const Query& qb = s->graphs[b].waiting.front();
+        return qa.t_arrival != qb.t_arrival ? qa.t_arrival < qb.t_arrival : qa.ticket < qb.ticket;
+      });
+    }
+    Context* c = nullptr;
+    for (int gid : order) {
+      const bfs_graph* g;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        g = s->graphs[gid].g;
+      }
+      if ((c = acquire_context(s, gid, g))) break;
+    }
+    if (!c) return;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      std::deque<Query>& w = s->graphs[c->gid].waiting;
+      while (!w.empty() && (int)c->q.size() < s->opt.max_lanes) {
+        c->q.push_back(w.front());
+        w.pop_front();
+      }
+      s->waiting -= (int64_t)c->q.size();
+      s->in_flight += 1;
+      s->launches += 1;
+      s->lanes += (int64_t)c->q.size();
+    }
+    launch(s, *c);
+  }
+}
+
+void worker_main(bfs_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    reap(s);
+    schedule(s);
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->stop && s->in_flight == 0) break;
+    s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->wake; });
+    s->wake = false;
+  }
+  s->cv_done.notify_all();
+}
+
+}  // namespace
+
+extern "C" void bfs_server_options_default(bfs_server_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->max_concurrent = 2;
+  opt->max_lanes = kMaxLanes;
+  opt->with_parents = 1;
+  opt->contexts_per_graph = 2;
+}
+
+extern "C" int64_t bfs_server_now_ns(void) { return now_ns(); }
+
+extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out) {
+  if (!out) return fail(BFS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  bfs_server_options o;
+  if (opt) o = *opt;
+  else bfs_server_options_default(&o);
+  if (o.max_concurrent == 0) o.max_concurrent = 2;
+  if (o.max_lanes == 0) o.max_lanes = kMaxLanes;
+  if (o.contexts_per_graph == 0) o.contexts_per_graph = o.max_concurrent;
+  if (o.max_concurrent < 1 || o.max_concurrent > kMaxConcurrent) return fail(BFS_ERR_INVALID, "max_concurrent must be 1..8");
+  if (o.max_lanes < 1 || o.max_lanes > kMaxLanes) return fail(BFS_ERR_INVALID, "max_lanes must be 1..64");
+  if (o.contexts_per_graph < 1 || o.contexts_per_graph > o.max_concurrent)
+    return fail(BFS_ERR_INVALID, "contexts_per_graph must be 1..max_concurrent");
+  if (o.with_parents != 0 && o.with_parents != 1) return fail(BFS_ERR_INVALID, "with_parents must be 0 or 1");
+  if (o.hbm_reserve_bytes < 0 || o.hbm_budget_bytes < 0) return fail(BFS_ERR_INVALID, "byte limits must be >= 0");
+  int dev = 0, cap = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs_server_create");
+  int rc = bfs_batch_capacity(&cap);
+  if (rc) return rc;
+  if (cap / o.max_concurrent < 1) return fail(BFS_ERR_INVALID, "max_concurrent exceeds the device's CTA capacity");
+  bfs_server* s = new (std::nothrow) bfs_server();
+  if (!s) return fail(BFS_ERR_OOM, "host allocation failed");
+  s->opt = o;
+  s->device = dev;
+  s->capacity = cap;
+  s->slice = cap / o.max_concurrent;
+  try {
+    s->worker = std::thread(worker_main, s);
+  } catch (...) {
+    delete s;
+    return fail(BFS_ERR_OOM, "cannot start the worker thread");
+  }
+  *out = s;
+  return BFS_OK;
+}
+
+extern "C" int bfs_server_add_graph(bfs_server* s, const bfs_graph* g, int32_t* graph_id) {
+  if (!s || !g || !graph_id) return fail(BFS_ERR_INVALID, "server, graph or graph_id is NULL");
+  if (g->device != s->device) return fail(BFS_ERR_INVALID, "the graph lives on another device than the server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return fail(BFS_ERR_INVALID, "the server is stopping");
+  s->graphs.push_back(GraphEntry{g, {}});
+  *graph_id = (int32_t)s->graphs.size() - 1;
+  return BFS_OK;
+}
+
+extern "C" int bfs_server_submit(bfs_server* s, int32_t graph_id, int32_t source, uint8_t* depth, int32_t* parent,
+                                 int64_t t_arrival_ns, int64_t* ticket) {
+  if (!s || !depth || !ticket) return fail(BFS_ERR_INVALID, "server, depth or ticket is NULL");
+  if ((parent != nullptr) != (s->opt.with_parents == 1))
+    return fail(BFS_ERR_INVALID, s->opt.with_parents ? "this server needs a parent buffer" : "this server writes no parents");
+  if (!device_ptr(depth) || (parent && !device_ptr(parent)))
+    return fail(BFS_ERR_INVALID, "depth and parent must be device buffers");
+  const int64_t t = t_arrival_ns ? t_arrival_ns : now_ns();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return fail(BFS_ERR_INVALID, "the server is stopping");
+    if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size()) return fail(BFS_ERR_INVALID, "unknown graph id");
+    GraphEntry& ge = s->graphs[graph_id];
+    if (source < 0 || source >= ge.g->n) return fail(BFS_ERR_INVALID, "source out of range");
+    *ticket = s->next_ticket++;
+    ge.waiting.push_back(Query{*ticket, source, depth, parent, t});
+    s->waiting += 1;
+    s->submitted += 1;
+    s->wake = true;
+  }
+  s->cv_work.notify_one();
+  return BFS_OK;
+}
+
+extern "C" int bfs_server_poll(bfs_server* s, bfs_server_done* done, int32_t max_done, int32_t timeout_ms,
+                               int32_t* n_done) {
+  if (!s || !n_done || (max_done > 0 && !done)) return fail(BFS_ERR_INVALID, "server, done or n_done is NULL");
+  *n_done = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->done.empty() && timeout_ms != 0) {
+    auto ready = [&] { return !s->done.empty() || (s->waiting == 0 && s->in_flight == 0) || s->stop; };
+    if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+    else s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  }
+  int32_t n = 0;
+  while (n < max_done && !s->done.empty()) {
+    done[n++] = s->done.front();
+    s->done.pop_front();
+  }
+  *n_done = n;
+  return BFS_OK;
+}
+
+extern "C" int bfs_server_get_stats(bfs_server* s, bfs_server_stats* st) {
+  if (!s || !st) return fail(BFS_ERR_INVALID, "server or stats is NULL");
+  std::memset(st, 0, sizeof(*st));
+  std::lock_guard<std::mutex> lk(s->mu);
+  st->submitted = s->submitted;
+  st->completed = s->completed;
+  st->failed = s->failed;
+  st->launches = s->launches;
+  st->lanes_launched = s->lanes;
+  st->contexts_created = s->created;
+  st->contexts_evicted = s->evicted;
+  st->context_bytes = s->ctx_bytes;
+  st->waiting = s->waiting;
+  st->in_flight = s->in_flight;
+  st->capacity_ctas = s->capacity;
+  st->ctas_per_launch = s->slice;
+  return BFS_OK;
+}
+
+extern "C" void bfs_server_destroy(bfs_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->wake = true;
+  }
+  s->cv_work.notify_all();
+  s->cv_done.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  while (!s->ctx.empty()) drop_context(s, s->ctx.size() - 1);
+  delete s;
+}
+
+extern "C" void bfs_server_abi_sizes(int64_t sizes[3]) {
+  if (!sizes) return;
+  sizes[0] = (int64_t)sizeof(bfs_server_options);
+  sizes[1] = (int64_t)sizeof(bfs_server_done);
+  sizes[2] = (int64_t)sizeof(bfs_server_stats);
+}

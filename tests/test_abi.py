@@ -15,7 +15,7 @@ def _declared():
         if f.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", f)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            for m in re.finditer(r"^\s*(?:int|void|const char\*)\s+(bfs_\w+)\s*\(", txt, flags=re.M):
+            for m in re.finditer(r"^\s*(?:int|int64_t|void|const char\*)\s+(bfs_\w+)\s*\(", txt, flags=re.M):
                 names.add(m.group(1))
     return names
 
@@ -59,3 +59,22 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.h" not in txt and "liboracle" not in txt, f
+
+
+def test_server_argument_checks_without_gpu():
+    import paper_1803_03922_gb300 as bfs
+
+    lib = bfs._load()
+    o = bfs.bfs_server_options_default()
+    assert (o.max_concurrent, o.max_lanes, o.with_parents) == (2, 64, 1)
+    h = ctypes.c_void_p()
+    for field, bad in (("max_lanes", 65), ("max_concurrent", 9), ("with_parents", 2), ("hbm_budget_bytes", -1)):
+        o2 = bfs.bfs_server_options_default()
+        setattr(o2, field, bad)
+        assert lib.bfs_server_create(ctypes.byref(o2), ctypes.byref(h)) == bfs.BFS_ERR_INVALID, field
+    t = ctypes.c_int64()
+    assert lib.bfs_server_submit(None, 0, 0, None, None, 0, ctypes.byref(t)) == bfs.BFS_ERR_INVALID
+    n = ctypes.c_int32()
+    assert lib.bfs_server_poll(None, None, 0, 0, ctypes.byref(n)) == bfs.BFS_ERR_INVALID
+    lib.bfs_server_destroy(None)
+    assert bfs.bfs_server_now_ns() > 0

@@ -95,6 +95,32 @@ def test_batch_rmat16_64_sources():
     _batch_check(og, g, sources[:33], host=True)
 
 
+@pytest.mark.parametrize("ctas", [1, 37, 152])
+def test_batch_grid_sizes(ctas):
+    """A context may take any CTA count up to the co-resident capacity (the
+    serving loop runs several such launches side by side)."""
+    torch = need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    scale = 14
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=14)
+    og = oracle.Graph(n, src, dst)
+    g = gpu_graph(n, src, dst, th=32)
+    assert ctas <= bfs.bfs_batch_capacity()
+    sources = np.random.default_rng(ctas).integers(0, n, 40)
+    want_d, want_p = og.bfs_batch_u8(sources)
+    b = bfs.Batch(g, ctas=ctas)
+    for k in (1, 3, 40):  # lane strides 4, 4, 40
+        d, p = b.run(sources[:k])
+        for j in range(k):
+            assert_same(d[j].cpu().numpy(), want_d[j], "depth, %d CTAs, lane %d of %d" % (ctas, j, k))
+            assert_same(p[j].cpu().numpy(), want_p[j], "parent, %d CTAs, lane %d of %d" % (ctas, j, k))
+    with pytest.raises(bfs.BfsError):
+        bfs.Batch(g, ctas=bfs.bfs_batch_capacity() + 1)
+    b.close()
+
+
 def test_batch_isolated_and_overflow():
     torch = need_cuda()
     import paper_1803_03922_gb300 as bfs
@@ -110,3 +136,5 @@ def test_batch_isolated_and_overflow():
     d, p, st = b.run([150], stats=True)  # the context stays usable
     dn = d.cpu().numpy()
     assert int(dn[dn != 255].max()) == 150 and st.levels == 151
+    d, p, st = b.run([301, 301], stats=True)  # isolated sources only: depth 0 is the deepest
+    assert st.levels == 1 and st.logged_levels == 0 and st.pairs_reached == 0
