@@ -35,8 +35,18 @@ struct __align__(64) MsSlot {
   unsigned long long pdeg;   // sum over those pairs of the degree
   unsigned long long nch;    // delegate chunk entries of the frontier
   unsigned long long mdone;  // degree of vertices every active lane has now reached
-  unsigned long long pad[2];
+  unsigned long long ndl;    // deferred row chunks of the backward level
+  unsigned long long aux;    // slot 0: lanes with a non-isolated source
 };
+
+// A chunk of a long row whose first kMsHead entries left some lane without a
+// parent: entries [head end + c * kChunk, + kChunk) of v's row, for lanes `need`.
+struct __align__(16) MsDefer {
+  int32_t v, c;
+  unsigned long long need;
+};
+
+constexpr int kMsHead = 512;
 
 struct MsLog {
   int32_t dir, pad;
@@ -57,6 +67,7 @@ struct MsParams {
   int32_t* parent_i;  // [n_ni][ls] or null
   int2* CL0;
   int2* CL1;
+  MsDefer* DL;        // deferred row chunks of a backward level [cl_cap]
   MsSlot* slot;       // [4]
   MsLog* log;         // [BFS_BATCH_LOG_LEVELS]
   RunHeader* hdr;
@@ -173,24 +184,39 @@ __device__ __forceinline__ void ms_found(const MsParams& p, int v, unsigned long
   }
 }
 
-__device__ void ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) {
+// Returns 1 in a thread that deferred row chunks.
+__device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) {
+  MsSlot* sc = p.slot + (L & 3);
+  int deferred = 0;
   const unsigned long long* Fc = Fbuf(p, L % 3);
   unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
   const int lane = lane_id();
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t gwarp = gtid >> 5, nwarps = gthreads >> 5;
-  // normal vertices: one thread per vertex, four row entries in flight per step
-  for (int64_t v = p.d + gtid; v < p.n_ni; v += gthreads) {
-    unsigned long long need = lanes & ~p.visit[v];
-    if (!need) continue;
-    const int64_t beg = p.off[v], end = beg + p.deg[v];
-    unsigned long long found = 0;
-    for (int64_t j = beg; j < end && need; j += 4) {
+  // normal vertices, 32 per warp (lane i owns vertex v0 + i).  Head: each owner
+  // checks the first four entries of its row.  Rest: the warp walks the rows'
+  // remaining entries 32 per step (consecutive rows are contiguous, so the column
+  // loads coalesce); a segmented OR-scan along the lanes gives each entry's new
+  // first hits, and an owner carries its vertex's found lanes from step to step.
+  const int64_t nbatch = ((int64_t)p.n_ni - p.d + 31) / 32;
+  for (int64_t it = gwarp; it < nbatch; it += nwarps) {  // warp-uniform
+    const int64_t v0 = p.d + it * 32;
+    const int64_t v = v0 + lane;
+    unsigned long long need = 0, found = 0;
+    int64_t beg = 0, end = 0;
+    if (v < p.n_ni) {
+      need = lanes & ~p.visit[v];
+      if (need) {
+        beg = p.off[v];
+        end = beg + p.deg[v];
+      }
+    }
+    if (need) {
       int u[4];
       unsigned long long h[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) u[t] = j + t < end ? __ldcs(p.col + j + t) : -1;
+      for (int t = 0; t < 4; ++t) u[t] = beg + t < end ? __ldcs(p.col + beg + t) : -1;
 #pragma unroll
       for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? Fc[u[t]] : 0ull;
 #pragma unroll
@@ -203,9 +229,54 @@ __device__ void ms_expand_bu(const MsParams& p, int L, unsigned long long lanes)
         }
       }
     }
+    const int64_t rb = beg + 4;
+    const int64_t rest = (need && end > rb) ? end - rb : 0;
+    const int64_t incl = warp_incl_scan(rest);
+    const int64_t total = __shfl_sync(kFull, incl, 31);
+    const int64_t excl = incl - rest;
+    for (int64_t base = 0; base < total; base += 32) {
+      if (!__any_sync(kFull, need != 0 && excl + rest > base)) break;
+      const int64_t e = base + lane;
+      int pos = 0;
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int64_t t = __shfl_sync(kFull, incl, pos + sh - 1);
+        if (t <= e) pos += sh;
+      }
+      const int64_t orb = __shfl_sync(kFull, rb, pos);
+      const int64_t oex = __shfl_sync(kFull, excl, pos);
+      const unsigned long long oneed = __shfl_sync(kFull, need, pos);
+      int u = -1;
+      unsigned long long h = 0;
+      if (e < total && oneed) {
+        u = __ldcs(p.col + orb + (e - oex));
+        h = Fc[u] & oneed;
+      }
+      unsigned long long sc = h;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(kFull, sc, o);
+        const int ps = __shfl_up_sync(kFull, pos, o);
+        if (lane >= o && ps == pos) sc |= t;
+      }
+      unsigned long long before = __shfl_up_sync(kFull, sc, 1);
+      const int pprev = __shfl_up_sync(kFull, pos, 1);
+      if (lane == 0 || pprev != pos) before = 0;
+      const unsigned long long nb = h & ~before;
+      if (nb) ms_found(p, (int)(v0 + pos), nb, u, L);
+      // this step's part of the owner's row: lanes [lo, hi) - base; its last lane
+      // holds the OR of the part
+      const int64_t lo = max(excl, base), hi = min(excl + rest, base + 32);
+      const unsigned long long tot = __shfl_sync(kFull, sc, hi > lo ? (int)(hi - 1 - base) : lane);
+      if (hi > lo) {
+        found |= tot;
+        need &= ~tot;
+      }
+    }
     if (found) Fn[v] = found;
   }
-  // delegates: one warp per vertex
+  // delegates: one warp per vertex over the first kMsHead entries of its row;
+  // what is left of a row with lanes still missing goes to the deferred list
   const int64_t items = ((int64_t)p.d + 31) / 32;
   for (int64_t it = gwarp; it < items; it += nwarps) {
     const int64_t v = it * 32 + lane;
@@ -218,14 +289,15 @@ __device__ void ms_expand_bu(const MsParams& p, int L, unsigned long long lanes)
       unsigned long long need = __shfl_sync(kFull, need_l, j);
       const int64_t beg = p.off[vv], end = beg + p.deg[vv];
       unsigned long long found = 0;
+      const int64_t al = beg & ~(int64_t)3, hend = min(end, al + kMsHead);
       // 128 entries per step: lane l holds entries 4l..4l+3 of the step (one
       // 128-bit load), in row order within the lane, lanes in order along the row
-      for (int64_t j0 = beg & ~(int64_t)3; j0 < end && need; j0 += 128) {
+      for (int64_t j0 = al; j0 < hend && need; j0 += 128) {
         const int64_t jj = j0 + 4 * lane;
         int4 c4 = make_int4(-1, -1, -1, -1);
-        if (jj < end) c4 = __ldcs(reinterpret_cast<const int4*>(p.col + jj));
-        const int u[4] = {jj >= beg ? c4.x : -1, (jj + 1 >= beg && jj + 1 < end) ? c4.y : -1,
-                          (jj + 2 >= beg && jj + 2 < end) ? c4.z : -1, (jj + 3 >= beg && jj + 3 < end) ? c4.w : -1};
+        if (jj < hend) c4 = __ldcs(reinterpret_cast<const int4*>(p.col + jj));
+        const int u[4] = {jj >= beg ? c4.x : -1, (jj + 1 >= beg && jj + 1 < hend) ? c4.y : -1,
+                          (jj + 2 >= beg && jj + 2 < hend) ? c4.z : -1, (jj + 3 >= beg && jj + 3 < hend) ? c4.w : -1};
         unsigned long long h[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? (Fc[u[t]] & need) : 0ull;
@@ -249,7 +321,78 @@ __device__ void ms_expand_bu(const MsParams& p, int L, unsigned long long lanes)
         need &= ~tot;
       }
       if (lane == 0 && found) Fn[vv] = found;
+      if (need && hend < end) {
+        const int nc = (int)((end - hend + kChunk - 1) / kChunk);
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&sc->ndl, (unsigned long long)nc);
+        base = __shfl_sync(kFull, base, 0);
+        for (int c = lane; c < nc; c += 32) {
+          MsDefer e;
+          e.v = vv;
+          e.c = c;
+          e.need = need;
+          p.DL[base + c] = e;
+        }
+        deferred = 1;
+      }
     }
+  }
+  return deferred;
+}
+
+// Deferred chunks of a backward level, after a grid barrier (the head scans'
+// found bits are in F_next).  Chunks of one row run on different warps, so a
+// lane's canonical parent (first hit in row order = smallest caller id) is the
+// atomicMin of the chunks' first hits, in caller ids as in forward levels.
+__device__ void ms_drain_bu(const MsParams& p, int L) {
+  const MsSlot* sc = p.slot + (L & 3);
+  const unsigned long long* Fc = Fbuf(p, L % 3);
+  unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
+  const int lane = lane_id();
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nd = (int64_t)__ldcg(&sc->ndl);
+  for (int64_t it = gwarp; it < nd; it += nwarps) {
+    const MsDefer e = p.DL[it];
+    const int v = e.v;
+    unsigned long long need = e.need, found = 0;
+    const int64_t beg = p.off[v], end = beg + p.deg[v];
+    const int64_t c0 = (beg & ~(int64_t)3) + kMsHead + (int64_t)e.c * kChunk;
+    const int64_t c1 = min(c0 + kChunk, end);
+    for (int64_t j0 = c0; j0 < c1 && need; j0 += 128) {
+      const int64_t jj = j0 + 4 * lane;
+      int4 c4 = make_int4(-1, -1, -1, -1);
+      if (jj < c1) c4 = __ldcs(reinterpret_cast<const int4*>(p.col + jj));
+      const int u[4] = {c4.x, jj + 1 < c1 ? c4.y : -1, jj + 2 < c1 ? c4.z : -1, jj + 3 < c1 ? c4.w : -1};
+      unsigned long long h[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? (Fc[u[t]] & need) : 0ull;
+      unsigned long long incl = h[0] | h[1] | h[2] | h[3];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl |= t;
+      }
+      unsigned long long before = __shfl_up_sync(kFull, incl, 1);
+      if (lane == 0) before = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        unsigned long long nb = h[t] & ~before;
+        before |= h[t];
+        if (!nb) continue;
+        const int pc = p.parent_i ? p.caller_of[u[t]] : 0;
+        while (nb) {
+          const int b = __ffsll((long long)nb) - 1;
+          nb &= nb - 1;
+          if (p.parent_i) atomicMin(p.parent_i + (int64_t)v * p.ls + b, pc);
+          p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
+        }
+      }
+      const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+      found |= tot;
+      need &= ~tot;
+    }
+    if (lane == 0 && found) atomicOr(Fn + v, found);
   }
 }
 
@@ -322,7 +465,7 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
   }
 }
 
-constexpr int kMsBackward = 1, kMsDone = 2;
+constexpr int kMsBackward = 1, kMsDone = 2, kMsDrain = 4;
 
 __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   __shared__ long long s_mu;
@@ -371,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     p.slot[0].nfv = nfv;
     p.slot[0].mfv = mfv;
     p.slot[0].nch = nch;
-    p.slot[0].pad[0] = act;
+    p.slot[0].aux = act;
     s_mu = (long long)p.nnz;
     s_pairs = 0;
     s_pdeg = pdeg;
@@ -379,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   int bits = grid_sync(p, seq, [&](int) { return p.slot[0].nfv ? 0 : kMsDone; });
   if (bits < 0) return;
   __shared__ unsigned long long s_tb, s_te;
-  const unsigned long long lanes = __ldcg(&p.slot[0].pad[0]);  // lanes with a non-isolated source
+  const unsigned long long lanes = __ldcg(&p.slot[0].aux);  // lanes with a non-isolated source
   const unsigned long long t_start = gtimer();
   if (leader) p.hdr->t_init = t_start;
   int L = 0;
@@ -387,11 +530,18 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     if (leader) s_tb = gtimer();
     if (threadIdx.x == 0 && (L > 300 || gtimer() - t_start > p.run_timeout_ns)) set_failed(p, BFS_ERR_TIMEOUT);
     const bool bu = (bits & kMsBackward) != 0;
-    if (bu)
-      ms_expand_bu(p, L, lanes);
-    else
+    if (bu) {
+      const int fl = ms_expand_bu(p, L, lanes);
+      const int b2 = grid_sync(p, seq, [](int f) { return (f & 1) ? kMsDrain : 0; }, fl);
+      if (b2 < 0) return;
+      if (b2 & kMsDrain) {
+        ms_drain_bu(p, L);
+        if (grid_sync(p, seq, no_master) < 0) return;
+      }
+    } else {
       ms_expand_td(p, L);
-    if (grid_sync(p, seq, no_master) < 0) return;
+      if (grid_sync(p, seq, no_master) < 0) return;
+    }
     if (leader) s_te = gtimer();
     ms_level_end(p, L, !bu, lanes);
     if (leader) p.slot[(L + 2) & 3] = MsSlot();
@@ -472,6 +622,7 @@ struct bfs_batch {
   uint8_t* depth_i = nullptr;
   int32_t* parent_i = nullptr;
   int2* CL = nullptr;  // 2 x cl_cap
+  bfsgb::MsDefer* DL = nullptr;  // cl_cap
   bfsgb::MsSlot* slot = nullptr;
   bfsgb::MsLog* log = nullptr;
   bfsgb::RunHeader* hdr = nullptr;
@@ -488,7 +639,7 @@ using namespace bfsgb;
 namespace {
 
 void batch_free_all(bfs_batch* b) {
-  void* ptrs[] = {b->visit, b->F, b->depth_i, b->parent_i, b->CL, b->slot, b->log, b->hdr, b->arrive,
+  void* ptrs[] = {b->visit, b->F, b->depth_i, b->parent_i, b->CL, b->DL, b->slot, b->log, b->hdr, b->arrive,
                   b->out_depth, b->out_parent};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -546,6 +697,7 @@ extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, int32_
   if (!rc) rc = balloc((void**)&b->depth_i, (size_t)kMsLanes * nn, b, "alloc batch depths");
   if (!rc && with_parents) rc = balloc((void**)&b->parent_i, (size_t)kMsLanes * nn * 4, b, "alloc batch parents");
   if (!rc) rc = balloc((void**)&b->CL, 2 * (size_t)g->cl_cap * sizeof(int2), b, "alloc chunk lists");
+  if (!rc) rc = balloc((void**)&b->DL, (size_t)g->cl_cap * sizeof(MsDefer), b, "alloc deferred chunks");
   if (!rc) rc = balloc((void**)&b->slot, 4 * sizeof(MsSlot), b, "alloc counters");
   if (!rc) rc = balloc((void**)&b->log, BFS_BATCH_LOG_LEVELS * sizeof(MsLog), b, "alloc batch log");
   if (!rc) rc = balloc((void**)&b->hdr, sizeof(RunHeader), b, "alloc header");
@@ -584,6 +736,7 @@ namespace bfsgb {
 int64_t ms_batch_bytes(const bfs_graph* g, int with_parents) {
   const int64_t nn = (int64_t)g->n_ni + 1;
   return nn * 8 * 4 + (int64_t)kMsLanes * nn * (with_parents ? 5 : 1) + 2 * (int64_t)g->cl_cap * 8 +
+         (int64_t)g->cl_cap * (int64_t)sizeof(MsDefer) +
          4 * (int64_t)sizeof(MsSlot) + BFS_BATCH_LOG_LEVELS * (int64_t)sizeof(MsLog) + (int64_t)sizeof(RunHeader) +
          (int64_t)kMaxBlocks * 32;
 }
@@ -616,6 +769,7 @@ int ms_launch(bfs_batch* b, const int32_t* sources, int k, uint8_t* const* depth
   p.parent_i = parent ? b->parent_i : nullptr;
   p.CL0 = b->CL;
   p.CL1 = b->CL + g->cl_cap;
+  p.DL = b->DL;
   p.slot = b->slot;
   p.log = b->log;
   p.hdr = b->hdr;

@@ -121,6 +121,35 @@ def test_batch_grid_sizes(ctas):
     b.close()
 
 
+@pytest.mark.parametrize("th", [16, 64])
+def test_batch_deferred_long_rows(th):
+    """Backward levels split a long row past its first 512 entries into chunks run
+    by different warps: the canonical parent is then the smallest first hit over
+    the chunks.  Hub 0 has leaves 1..3000 (its row in caller order); each query's
+    source hangs off one or two leaves, so at level 1 the hub's only frontier
+    neighbours sit inside the head, in one deferred chunk, or in two chunks."""
+    need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    n_leaf = 3000
+    e = [(0, x) for x in range(1, n_leaf + 1)]
+    attach = [[100], [700], [2000, 700], [2999], [1500, 2600], [513], [514, 1030], [3000, 5]]
+    n = n_leaf + 1 + len(attach)
+    for j, xs in enumerate(attach):
+        e += [(n_leaf + 1 + j, x) for x in xs]
+    e = np.asarray(e, np.int32)
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th, alpha=1 << 30)  # backward from level 1 on
+    sources = [n_leaf + 1 + j for j in range(len(attach))]
+    _batch_check(og, g, sources)
+    _, want_p = og.bfs_batch_u8(sources)
+    assert [int(want_p[j][0]) for j in range(len(attach))] == [min(xs) for xs in attach]
+    b = bfs.Batch(g)
+    _, _, st = b.run(sources, stats=True)
+    assert [st.level[i].direction for i in range(st.logged_levels)][:2] == [0, 1]
+    b.close()
+
+
 def test_batch_isolated_and_overflow():
     torch = need_cuda()
     import paper_1803_03922_gb300 as bfs
