@@ -153,14 +153,17 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+LEVEL_LOOP_SOURCES = ("bfs_internal.cuh", "bfs_run.cu", "device_common.cuh")
+
+
 def kernel_source_sha():
+    """Digest of the sources that define the level-loop kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1803_03922_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode())
-                h.update(fh.read())
+    for f in LEVEL_LOOP_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -579,7 +582,7 @@ def config_of(name, w, info=None):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
