@@ -66,6 +66,8 @@ def _bind(lib):
     lib.orc_subgraph_counts.argtypes = [P, i64, P]
     lib.orc_level_counters.restype = ctypes.c_int
     lib.orc_level_counters.argtypes = [P, i32, P, i64, i32, P, P]
+    lib.orc_directions.restype = ctypes.c_int
+    lib.orc_directions.argtypes = [P, i32, P, i32, i64, i64, ctypes.c_double, ctypes.c_double, i32, P]
     return lib
 
 
@@ -173,6 +175,20 @@ class Graph:
         if rc:
             raise ValueError("orc_level_counters failed with code %d" % rc)
         return out
+
+    def directions(self, s: int, depth, rule: str = "beamer", alpha: int = 15, beta: int = 18,
+                   factor0: float = 0.5, factor1: float = 1e-7):
+        """Per-level directions (0 forward, 1 backward) that the rule ("beamer" or
+        "paper", Sec. IV-B) takes on the run from s with final depth `depth`."""
+        depth = np.ascontiguousarray(depth, dtype=np.int32)
+        cap = int(depth.max()) + 2 if depth.size else 1
+        out = np.zeros(cap, dtype=np.int32)
+        code = {"beamer": 0, "paper": 1}[rule]
+        rc = self._lib.orc_directions(self._h, int(s), _ptr(depth), code, int(alpha), int(beta), float(factor0),
+                                      float(factor1), cap, _ptr(out))
+        if rc < 0:
+            raise ValueError("orc_directions failed with code %d" % rc)
+        return out[:rc].copy()
 
     def subgraph_counts(self, th: int):
         """Directed entry counts (|E_nn|, |E_nd|, |E_dn|, |E_dd|) for threshold th (Sec. IV)."""

@@ -318,3 +318,55 @@ int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int6
   }
   return ORC_OK;
 }
+
+int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t rule, int64_t alpha, int64_t beta,
+                   double factor0, double factor1, int32_t max_levels, int32_t* dirs) {
+  if (!g || !depth || !dirs || s < 0 || s >= g->n || max_levels < 0) return ORC_ERR_INVALID;
+  if (rule != ORC_RULE_BEAMER && rule != ORC_RULE_PAPER) return ORC_ERR_INVALID;
+  if (g->off[s + 1] == g->off[s]) return 0; /* isolated source: no level runs */
+  int32_t levels = 0;
+  int64_t n_ni = 0;
+  for (int32_t v = 0; v < g->n; ++v) {
+    if (g->off[v + 1] > g->off[v]) n_ni += 1;
+    if (depth[v] + 1 > levels) levels = depth[v] + 1;
+  }
+  int64_t* q = calloc((size_t)levels + 1, sizeof(int64_t));
+  int64_t* fv = calloc((size_t)levels + 1, sizeof(int64_t));
+  if (!q || !fv) {
+    free(q);
+    free(fv);
+    return ORC_ERR_OOM;
+  }
+  int64_t m_total = 0;
+  for (int32_t v = 0; v < g->n; ++v) {
+    const int64_t deg = g->off[v + 1] - g->off[v];
+    m_total += deg;
+    if (depth[v] >= 0) {
+      q[depth[v]] += 1;
+      fv[depth[v]] += deg;
+    }
+  }
+  int cur = 0;
+  int64_t seen_v = 0, seen_m = 0;
+  for (int32_t L = 0; L < levels; ++L) {
+    seen_v += q[L];
+    seen_m += fv[L];
+    const int64_t s_u = n_ni - seen_v, m_u = m_total - seen_m;
+    const int64_t q_prev = L == 0 ? 1 : q[L - 1];
+    int next;
+    if (rule == ORC_RULE_PAPER) {
+      const double qd = (double)q[L], sd = (double)(s_u > 0 ? s_u : 0);
+      const double fvd = (double)fv[L], bv = sd * (qd + sd) / qd;
+      next = cur == 0 ? (fvd > factor0 * bv) : !(fvd < factor1 * bv);
+    } else if (cur == 0) {
+      next = fv[L] * alpha > m_u;
+    } else {
+      next = !(q[L] * beta < (int64_t)g->n && q[L] < q_prev);
+    }
+    cur = next ? 1 : 0;
+    if (L < max_levels) dirs[L] = cur;
+  }
+  free(q);
+  free(fv);
+  return levels;
+}

@@ -99,6 +99,28 @@ void orc_subgraph_counts(const orc_graph* g, int64_t th, int64_t counts[4]);
 int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int64_t th, int32_t levels,
                        const int32_t* dirs, int64_t* out);
 
+#define ORC_RULE_BEAMER 0
+#define ORC_RULE_PAPER 1
+
+/* Visit directions a direction rule takes on the run from s, given that run's
+ * final depth.  The direction of level L (which expands F_L, the vertices at
+ * depth L) is decided before it runs, from the current direction (level L-1's,
+ * forward before level 0) and these counts:
+ *   q   = |F_L|,  FV = sum of degrees over F_L,  q_prev = |F_{L-1}| (1 at L = 0),
+ *   s_u = non-isolated vertices not in F_0..F_L (not visited yet),
+ *   m_u = sum of their degrees,  n = the number of vertices.
+ * ORC_RULE_PAPER (Sec. IV-B): BV = |U| (q + s) / q with U and s both the
+ *   unvisited vertices (one symmetric graph), in double as s_u * (q + s_u) / q;
+ *   forward turns backward when FV > factor0 * BV, backward turns forward when
+ *   FV < factor1 * BV.
+ * ORC_RULE_BEAMER (Beamer's rule, which the paper's DO follows, Sec. II-C):
+ *   forward turns backward when alpha * FV > m_u; backward turns forward when
+ *   beta * q < n and q < q_prev.
+ * Writes dirs[L] (0 forward, 1 backward) for L < levels = max depth + 1, at
+ * most max_levels of them; returns levels (0 for an isolated source) or an error. */
+int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t rule, int64_t alpha, int64_t beta,
+                   double factor0, double factor1, int32_t max_levels, int32_t* dirs);
+
 #ifdef __cplusplus
 }
 #endif

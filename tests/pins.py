@@ -403,12 +403,65 @@ def pin_level_counters_closed_forms(lib):
     return ok and c2[0][6] == 1 and list(c2[1][3:5]) == [0, 0]
 
 
+def pin_directions_worked(lib):
+    """Both direction rules against the hand-worked levels of
+    tests/golden/directions_worked.txt (Sec. IV-B)."""
+    from tests.golden_io import read_directions
+
+    graphs, cases = read_directions()
+    built = {k: oracle.Graph(n, s, d, lib=lib) for k, (n, s, d) in graphs.items()}
+    for gname, src, rule, a, b, want in cases:
+        g = built[gname]
+        d, _ = g.bfs(src)
+        if rule == "paper":
+            got = g.directions(src, d, "paper", factor0=a, factor1=b)
+        else:
+            got = g.directions(src, d, "beamer", alpha=int(a), beta=int(b))
+        if list(got) != want:
+            return False
+    return True
+
+
+def pin_directions_limits(lib, seed=17):
+    """Limit cases of the rules on random graphs: factor0 = 0 goes backward at
+    level 0 and (factor1 = 0) never returns; factor0 = inf or alpha = 0 never
+    leaves forward; lowering factor0 or raising alpha never delays the first
+    backward level."""
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        n = int(rng.integers(2, 80))
+        e = rng.integers(0, n, (int(rng.integers(1, 4 * n)), 2)).astype(np.int32)
+        g = oracle.Graph(n, e[:, 0], e[:, 1], lib=lib)
+        s = int(e[0, 0]) if e[0, 0] != e[0, 1] else int(rng.integers(0, n))
+        d, _ = g.bfs(s)
+        levels = int(d.max()) + 1 if (g.csr()[0][s + 1] > g.csr()[0][s]) else 0
+        if levels == 0:
+            continue
+        if list(g.directions(s, d, "paper", factor0=0.0, factor1=0.0)) != [1] * levels:
+            return False
+        if list(g.directions(s, d, "paper", factor0=float("inf"), factor1=0.0)) != [0] * levels:
+            return False
+        if list(g.directions(s, d, "beamer", alpha=0, beta=18)) != [0] * levels:
+            return False
+
+        def first_b(x):
+            x = list(x)
+            return x.index(1) if 1 in x else levels
+
+        fp = [first_b(g.directions(s, d, "paper", factor0=f, factor1=0.0)) for f in (4.0, 1.0, 0.5, 0.1, 0.01)]
+        fb = [first_b(g.directions(s, d, "beamer", alpha=a, beta=18)) for a in (1, 4, 15, 60, 1000)]
+        if fp != sorted(fp, reverse=True) or fb != sorted(fb, reverse=True):
+            return False
+    return True
+
+
 PINS = [
     pin_path_end, pin_path_middle, pin_star, pin_grid, pin_binary_tree, pin_complete,
     pin_even_cycle, pin_components_and_isolated, pin_dedup_selfloops, pin_exhaustive_5,
     pin_random_small_floyd, pin_scipy_depth_components, pin_invariants_python,
     pin_validator_detects, pin_component_edges, pin_builder_sets, pin_separation,
-    pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms,
+    pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms, pin_directions_worked,
+    pin_directions_limits,
 ]
 
 

@@ -38,6 +38,11 @@ MUTANTS = [
     ("validator_no_canonical", "if (u < p && depth[u] == depth[v] - 1) return 6;", ""),
     ("validator_no_cut", "if ((depth[u] >= 0) != (depth[v] >= 0)) return 2;", ""),
     ("subgraph_source_only", "counts[(u_del << 1) | v_del] += 1;", "counts[(u_del << 1) | u_del] += 1;"),
+    ("paper_bv_swapped", "bv = sd * (qd + sd) / qd;", "bv = qd * (qd + sd) / sd;"),
+    ("paper_back_flipped", "!(fvd < factor1 * bv)", "!(fvd > factor1 * bv)"),
+    ("beamer_no_shrink_test", "q[L] * beta < (int64_t)g->n && q[L] < q_prev", "q[L] * beta < (int64_t)g->n"),
+    ("beamer_mu_all_edges", "m_u = m_total - seen_m;", "m_u = m_total;"),
+    ("directions_seen_after", "    seen_v += q[L];\n    seen_m += fv[L];\n", ""),
 ]
 
 
