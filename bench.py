@@ -549,6 +549,15 @@ def serving_bench(stream, rates=SERVE_RATES, duration_s=1.5, single_cap=2000, ma
     return out
 
 
+DEGREE_THS = (2, 4, 8, 16, 32, 64, 128, 256, 512, 1024)
+
+
+def degree_table(rows):
+    """Compact rows of Graph.degree_classes: TH, delegate % of vertices, nn/nd/dd % of entries."""
+    return [[r["th"], round(r["delegate_pct"], 4), round(r["nn_pct"], 3), round(r["nd_pct"], 3),
+             round(r["dd_pct"], 3)] for r in rows]
+
+
 def serving_extras(stream):
     out = {}
     try:
@@ -677,35 +686,43 @@ def main():
     host_edges = dw.host_edges
     sources = dw.sources
     ce_dev = dw.ce
+    degree_rows = dw.g.degree_classes(DEGREE_THS)
     dw.close()
     del dw
 
     if rank == 0 and not args.no_extras:
-        extras = {}
-        for th in (32, 128, 256):
-            if args.workload != "rmat22":
-                break
+        from paper_1803_03922_gb300.autotune import th_for_scale, th_space_for_scale
+
+        extras = {"degree_classes_%s" % args.workload: degree_table(degree_rows),
+                  "th_rule": {"rule": "64 * 2^((scale - 30) / 2) (Sec. VI-B)",
+                              "th_by_scale": {str(sc): th_for_scale(sc) for sc in (16, 22, 24, 26, 30, 32)}}}
+        for th in th_space_for_scale(w["scale"]):
+            if args.workload != "rmat22" or th == w["th"]:
+                continue
             d2 = DeviceWorkload("rmat22", w, rank, th=th)
             t2 = d2.timed(1, flush, stream)
             extras["rmat22_th%d" % th] = {"gteps": hmean(d2.gteps(t2)), "delegates": d2.info.delegates,
                                           "roofline_frac": sum(d2.model) / sum(t2) / 1e9 / peak}
             d2.close()
-        for name in ("rmat26", "er26"):
+        for key, name, th26 in (("rmat26", "rmat26", None), ("er26", "er26", None),
+                                ("rmat26_th%d" % th_for_scale(26), "rmat26", th_for_scale(26))):
             try:
-                d3 = DeviceWorkload(name, WORKLOADS[name], rank)
+                d3 = DeviceWorkload(name, WORKLOADS[name], rank, th=th26)
                 d3.timed(1, None, stream)
                 t3 = d3.timed(2, None, stream)
-                extras[name] = {"gteps": hmean(d3.gteps(t3)), "ms_per_bfs_median": 1e3 * statistics.median(t3),
+                extras[key] = {"gteps": hmean(d3.gteps(t3)), "ms_per_bfs_median": 1e3 * statistics.median(t3),
                                 "roofline_frac": sum(d3.model[i % len(d3.sources)] for i in range(len(t3)))
                                 / sum(t3) / 1e9 / peak,
                                 "nnz": d3.info.nnz, "delegates": d3.info.delegates,
                                 "levels": statistics.median(d3.levels), "build_s": d3.build_s,
                                 "directions_first_source": d3.dirs[0]}
+                if key == "rmat26":
+                    extras["degree_classes_rmat26"] = degree_table(d3.g.degree_classes(DEGREE_THS))
                 d3.close()
                 del d3
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not hide
-                extras[name] = {"error": str(e)}
+                extras[key] = {"error": str(e)}
         if not args.no_serving:
             extras.update(serving_extras(stream))
         line["extras"] = extras

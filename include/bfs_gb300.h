@@ -328,6 +328,19 @@ int bfs_wait(bfs_graph* g, struct CUstream_st* stream);
 int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_t n, int32_t source, int32_t* depth,
                    int32_t* parent, struct CUstream_st* stream);
 
+/* Degree-class statistics of a built graph for `count` thresholds (Sec. VI-B:
+ * TH balances the delegates against the nn edges; Figs. 5 and 7 plot both).  The
+ * graph's own TH does not matter: degrees are those of the deduplicated
+ * symmetric graph.  For ths[i] (>= 0), out[5*i + j] (host int64) is
+ *   j = 0 delegates (vertices of degree > ths[i]), 1 |E_nn|, 2 |E_nd|, 3 |E_dn|,
+ *   4 |E_dd| (directed entries whose source/destination are normal (n) or
+ *   delegate (d) under ths[i], Sec. IV).
+ * Allocates 24 bytes per possible degree on the device for the call and
+ * synchronizes `stream`.  Errors: INVALID (null, count < 1, a negative
+ * threshold), CUDA. */
+int bfs_degree_class_stats(const bfs_graph* g, const int64_t* ths, int32_t count, int64_t* out,
+                           struct CUstream_st* stream);
+
 /* Releases every device and host resource of the graph.  NULL is a no-op. */
 void bfs_free(bfs_graph* g);
 

@@ -142,6 +142,7 @@ def _load():
     lib.bfs_batch_wait.argtypes = [c_vp, c_vp]
     lib.bfs_batch_free.argtypes = [c_vp]
     lib.bfs_batch_free.restype = None
+    lib.bfs_degree_class_stats.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp]
     lib.bfs_server_options_default.argtypes = [ctypes.POINTER(bfs_server_options)]
     lib.bfs_server_options_default.restype = None
     lib.bfs_server_create.argtypes = [ctypes.POINTER(bfs_server_options), ctypes.POINTER(c_vp)]
@@ -310,6 +311,14 @@ def bfs_batch_free(b):
         _load().bfs_batch_free(b)
 
 
+def bfs_degree_class_stats(g, ths, stream=None):
+    """[len(ths), 5] int64: delegates, |E_nn|, |E_nd|, |E_dn|, |E_dd| per threshold."""
+    t = np.ascontiguousarray(ths, dtype=np.int64)
+    out = np.zeros((t.size, 5), dtype=np.int64)
+    _check(_load().bfs_degree_class_stats(g, _ptr(t), t.size, _ptr(out), _stream(stream)))
+    return out
+
+
 def bfs_server_options_default() -> bfs_server_options:
     o = bfs_server_options()
     _load().bfs_server_options_default(ctypes.byref(o))
@@ -407,6 +416,19 @@ class Graph:
 
     def wait(self, stream=None):
         bfs_wait(self._h, stream)
+
+    def degree_classes(self, ths, stream=None):
+        """Per threshold: delegates and their share of the vertices, and the nn/nd/dn/dd
+        shares of the directed entries, in percent (the quantities of Figs. 5 and 7)."""
+        st = bfs_degree_class_stats(self._h, ths, stream)
+        nnz = max(int(self.info.nnz), 1)
+        out = []
+        for th, (d, nn, nd, dn, dd) in zip(ths, st.tolist()):
+            out.append({"th": int(th), "delegates": d, "delegate_pct": 100.0 * d / self.n,
+                        "nn": nn, "nd": nd, "dn": dn, "dd": dd,
+                        "nn_pct": 100.0 * nn / nnz, "nd_pct": 100.0 * nd / nnz, "dn_pct": 100.0 * dn / nnz,
+                        "dd_pct": 100.0 * dd / nnz})
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -24,6 +24,26 @@ RUN_SPACE: Dict[str, Sequence] = {
 }
 PAPER_FACTOR0 = (0.05, 0.1, 0.5, 1.0, 2.0)
 TH_SPACE = (32, 64, 128, 256)
+
+
+def th_for_scale(scale: int) -> int:
+    """Degree threshold suggested for an RMAT graph of 2^scale vertices (Sec. VI-B):
+    the best TH grows by about sqrt(2) per scale, and 64 is the value taken at
+    scale 30 (128 at scale 32), so TH = 64 * 2^((scale - 30) / 2), rounded, >= 1."""
+    return max(1, int(round(64 * 2.0 ** ((scale - 30) / 2.0))))
+
+
+def th_goals(row: dict, n: int, p: int = 1) -> dict:
+    """The paper's two goals for TH (Sec. VI-B) on one row of Graph.degree_classes:
+    delegates under 4 n / p, and nn entries under 10 % of all entries."""
+    return {"delegates_under_4n_over_p": row["delegates"] <= 4 * n // p, "nn_under_10pct": row["nn_pct"] < 10.0}
+
+
+def th_space_for_scale(scale: int):
+    """TH candidates: the fixed sweep plus the per-scale rule's value and its
+    neighbours a factor 2 away."""
+    t = th_for_scale(scale)
+    return tuple(sorted(set(TH_SPACE) | {max(1, t // 2), t, 2 * t}))
 BEAMER, PAPER, MASK = 0, 5, 4
 
 

@@ -62,3 +62,17 @@ def test_tuned_schedule_is_bit_exact():
         d, p = g.run(int(s))
         want_d, want_p = og.bfs(int(s))
         assert np.array_equal(d.cpu().numpy(), want_d) and np.array_equal(p.cpu().numpy(), want_p)
+
+
+def test_th_rule_per_scale():
+    """Sec. VI-B: about sqrt(2) per scale, 64 at scale 30 and 128 at scale 32."""
+    from paper_1803_03922_gb300.autotune import th_for_scale, th_goals, th_space_for_scale
+
+    assert th_for_scale(30) == 64 and th_for_scale(32) == 128 and th_for_scale(28) == 32
+    assert [th_for_scale(s) for s in (22, 24, 26)] == [4, 8, 16]
+    for s in range(10, 40):
+        assert th_for_scale(s + 2) in (2 * th_for_scale(s), 2 * th_for_scale(s) - 1, 2 * th_for_scale(s) + 1) \
+            or th_for_scale(s) == 1
+    assert 16 in th_space_for_scale(26) and 8 in th_space_for_scale(26) and 32 in th_space_for_scale(26)
+    row = {"delegates": 10, "nn_pct": 12.0}
+    assert th_goals(row, 100) == {"delegates_under_4n_over_p": True, "nn_under_10pct": False}
