@@ -220,11 +220,13 @@ void bfs_batch_free(bfs_batch* b);
  * Not in the paper, which runs one source at a time.  A server borrows graph
  * handles and owns a worker thread.  Submitted queries wait in one FIFO per
  * graph.  Whenever fewer than max_concurrent launches are in flight, the worker
- * takes the graph whose oldest waiting query arrived first, packs up to
- * max_lanes of that graph's waiting queries into one multi-source launch (the
- * kernel of bfs_run_batch, so each query gets exactly the result bfs_run_batch
- * gives it alone) on a stream of its own, and reports each query when its
- * launch ends.  Each launch gets capacity / max_concurrent CTAs, so all launches
+ * takes the graph whose oldest waiting query arrived first and launches its
+ * waiting queries on a stream of their own: a lone query runs the single-source
+ * level loop (bfs_run's kernel, on the graph's run state, at most one such run
+ * per graph at a time; with single_path = 1), several are packed, up to
+ * max_lanes, into one multi-source launch (bfs_run_batch's kernel).  Either way a
+ * query's result is its exact hop distance and canonical parent, the same as
+ * alone.  Each query is reported when its launch ends.  Each launch gets capacity / max_concurrent CTAs, so all launches
  * in flight are co-resident.  Batch contexts are created on demand (at most
  * contexts_per_graph per graph); a new context is admitted only when the
  * device's free memory less hbm_reserve_bytes covers it and the bytes of all
@@ -240,7 +242,8 @@ typedef struct bfs_server_options {
   int32_t contexts_per_graph; /* batch contexts per graph, 1..max_concurrent (0 = max_concurrent) */
   int64_t hbm_reserve_bytes;  /* device memory left free when a context is admitted */
   int64_t hbm_budget_bytes;   /* cap on the device bytes of all contexts held (0 = none) */
-  int32_t reserved[8];        /* zero */
+  int32_t single_path;        /* 1: a lone query of a graph runs the single-source level loop */
+  int32_t reserved[7];        /* zero */
 } bfs_server_options;
 
 typedef struct bfs_server_done {
@@ -264,7 +267,8 @@ typedef struct bfs_server_stats {
   int64_t in_flight;      /* launches running */
   int32_t capacity_ctas;  /* co-resident CTAs of the batched kernel on the device */
   int32_t ctas_per_launch;
-  int64_t reserved[4];
+  int64_t single_launches; /* launches of the single-source level loop (lone queries) */
+  int64_t reserved[3];
 } bfs_server_stats;
 
 void bfs_server_options_default(bfs_server_options* opt);
@@ -272,9 +276,10 @@ void bfs_server_options_default(bfs_server_options* opt);
 /* Creates a server on the current device.  Errors: INVALID (option out of range), CUDA, OOM. */
 int bfs_server_create(const bfs_server_options* opt, bfs_server** out);
 
-/* Registers a graph (borrowed: it must outlive the server and must not run
- * bfs_run concurrently with the server's launches).  *graph_id = 0, 1, ... */
-int bfs_server_add_graph(bfs_server* s, const bfs_graph* g, int32_t* graph_id);
+/* Registers a graph (borrowed: it must outlive the server; the server runs
+ * single-source runs on it, so the caller must not call bfs_run on it while the
+ * server lives).  *graph_id = 0, 1, ... */
+int bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id);
 
 /* Host monotonic clock in ns (the clock of every bfs_server_done time). */
 int64_t bfs_server_now_ns(void);

@@ -87,7 +87,7 @@ class bfs_batch_stats(ctypes.Structure):
 class bfs_server_options(ctypes.Structure):
     _fields_ = [("max_concurrent", c_i32), ("max_lanes", c_i32), ("with_parents", c_i32),
                 ("contexts_per_graph", c_i32), ("hbm_reserve_bytes", c_i64), ("hbm_budget_bytes", c_i64),
-                ("reserved", c_i32 * 8)]
+                ("single_path", c_i32), ("reserved", c_i32 * 7)]
 
 
 class bfs_server_done(ctypes.Structure):
@@ -100,7 +100,8 @@ class bfs_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_i64), ("completed", c_i64), ("failed", c_i64), ("launches", c_i64),
                 ("lanes_launched", c_i64), ("contexts_created", c_i64), ("contexts_evicted", c_i64),
                 ("context_bytes", c_i64), ("waiting", c_i64), ("in_flight", c_i64),
-                ("capacity_ctas", c_i32), ("ctas_per_launch", c_i32), ("reserved", c_i64 * 4)]
+                ("capacity_ctas", c_i32), ("ctas_per_launch", c_i32), ("single_launches", c_i64),
+                ("reserved", c_i64 * 3)]
 
 
 class BfsError(RuntimeError):
@@ -485,7 +486,8 @@ class Server:
     """Continuous-batching query server over device-resident Graphs (bfs_server_*)."""
 
     def __init__(self, max_concurrent: int = 2, max_lanes: int = 64, with_parents: bool = True,
-                 contexts_per_graph: int = 0, hbm_reserve_bytes: int = 0, hbm_budget_bytes: int = 0):
+                 contexts_per_graph: int = 0, hbm_reserve_bytes: int = 0, hbm_budget_bytes: int = 0,
+                 single_path: bool = True):
         o = bfs_server_options_default()
         o.max_concurrent = max_concurrent
         o.max_lanes = max_lanes
@@ -493,6 +495,7 @@ class Server:
         o.contexts_per_graph = contexts_per_graph
         o.hbm_reserve_bytes = hbm_reserve_bytes
         o.hbm_budget_bytes = hbm_budget_bytes
+        o.single_path = 1 if single_path else 0
         self.with_parents = with_parents
         self.graphs = []
         self._live = {}  # ticket -> (depth, parent) kept alive until reported

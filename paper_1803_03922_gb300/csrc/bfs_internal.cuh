@@ -77,8 +77,9 @@ struct BfsParams {
   LevelLogDev* log;          // [BFS_LOG_LEVELS]
   RunHeader* hdr;
   unsigned long long* arrive;// grid-barrier arrival words, one per CTA, 32 bytes apart
-  int32_t* out_depth;        // [n] caller-indexed
-  int32_t* out_parent;       // [n]
+  int32_t* out_depth;        // [n] caller-indexed (unused when out_depth8 is set)
+  int32_t* out_parent;       // [n] or null
+  uint8_t* out_depth8;       // [n] uint8 depth (255 unreached) instead of out_depth, or null
   int64_t nnz;
   int64_t words;             // ceil(n_ni / 32)
   int32_t n, n_ni, d;
@@ -143,7 +144,10 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 // Level-loop set-up and launch (bfs_run.cu).
 int configure_run(bfs_graph* g);
-int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s);
+// grid: CTAs of the cooperative launch (0 = the graph's full grid); out_depth8:
+// uint8 depths (255 unreached, BFS_ERR_OVERFLOW past 254) instead of out_depth.
+int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s, int grid = 0,
+               uint8_t* out_depth8 = nullptr);
 int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st);
 
 // Multi-source batches (msbfs.cu).  ms_batch_bytes: device bytes of a batch

@@ -959,7 +959,25 @@ __device__ void run_body(const BfsParams& p) {
       }
     }
     const int64_t c = q * 4;
-    if (p.out_vec4 && c + 3 < p.n) {
+    if (p.out_depth8) {  // uint8 form: 255 = unreached
+      unsigned d8 = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (dv[t] > 254) set_failed(p, BFS_ERR_OVERFLOW);
+        d8 |= (unsigned)(dv[t] < 0 ? 255 : (dv[t] & 0xFF)) << (8 * t);
+      }
+      if (p.out_vec4 && c + 3 < p.n) {
+        reinterpret_cast<unsigned*>(p.out_depth8)[q] = d8;
+        if (p.out_parent) reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (c + t < p.n) {
+            p.out_depth8[c + t] = (uint8_t)(d8 >> (8 * t));
+            if (p.out_parent) p.out_parent[c + t] = pv[t];
+          }
+      }
+    } else if (p.out_vec4 && c + 3 < p.n) {
       reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
       reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
     } else {
@@ -1001,7 +1019,8 @@ int configure_run(bfs_graph* g) {
   return BFS_OK;
 }
 
-int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s) {
+int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_parent, cudaStream_t s, int grid,
+               uint8_t* out_depth8) {
   BfsParams p;
   p.off = g->off;
   p.col = g->col;
@@ -1025,6 +1044,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.arrive = g->arrive;
   p.out_depth = out_depth;
   p.out_parent = out_parent;
+  p.out_depth8 = out_depth8;
   p.nnz = g->nnz;
   p.words = g->words;
   p.n = g->n;
@@ -1041,7 +1061,8 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.timeout_ns = (unsigned long long)g->opt.barrier_timeout_ms * 1000000ull;
   p.test_skip_barrier = g->opt.test_skip_barrier;
   p.run_timeout_ns = (unsigned long long)g->opt.run_timeout_ms * 1000000ull;
-  p.out_vec4 = ((((uintptr_t)out_depth) | ((uintptr_t)out_parent)) & 15) == 0;
+  p.out_vec4 = out_depth8 ? ((((uintptr_t)out_depth8) & 3) == 0 && (((uintptr_t)out_parent) & 15) == 0)
+                         : ((((uintptr_t)out_depth) | ((uintptr_t)out_parent)) & 15) == 0;
   p.tuning = g->opt.tuning;
   p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
@@ -1052,7 +1073,8 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   }
   void* args[] = {&p};
   const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3> : (const void*)bfs_level_loop<2>;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(g->grid_blocks), dim3(kThreads), args, 0, s);
+  const int blocks = grid > 0 && grid < g->grid_blocks ? grid : g->grid_blocks;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kThreads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
   return BFS_OK;
 }

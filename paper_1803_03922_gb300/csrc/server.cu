@@ -9,11 +9,14 @@
 // wait for queued host functions, which take `mu`).
 //
 // Scheduling: one FIFO per graph.  While fewer than max_concurrent launches run,
-// the graph whose oldest waiting query arrived first gets an idle context (or a
+// the graph whose oldest waiting query arrived first gets one launch of up to
+// max_lanes of its waiting queries: a lone query runs the single-source level
+// loop on the graph's own run state (when no other single run of that graph is
+// in flight), several share a multi-source batch on an idle batch context (or a
 // new one, if free device memory and the budget admit it, after freeing idle
-// contexts of other graphs least recently used first) and one launch of up to
-// max_lanes of its waiting queries.  Every launch has capacity / max_concurrent
-// CTAs, so the cooperative launches in flight always fit on the device together.
+// contexts of other graphs least recently used first).  Every launch has
+// capacity / max_concurrent CTAs, so the cooperative launches in flight always
+// fit on the device together.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -52,14 +55,15 @@ struct Query {
 };
 
 struct GraphEntry {
-  const bfs_graph* g;
+  bfs_graph* g;
   std::deque<Query> waiting;
 };
 
 struct Context {
   bfs_server* srv = nullptr;
   int gid = 0;
-  bfs_batch* b = nullptr;
+  bool single = false;     // runs the single-source level loop on the graph's run state
+  bfs_batch* b = nullptr;  // batch contexts only
   cudaStream_t stream = nullptr;
   RunHeader* hdr = nullptr;  // pinned host copy of the launch's run header
   int64_t bytes = 0;
@@ -95,7 +99,7 @@ struct bfs_server {
   int64_t waiting = 0;
   int in_flight = 0;
   bool stop = false, wake = false;
-  int64_t submitted = 0, completed = 0, failed = 0, launches = 0, lanes = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, launches = 0, lanes = 0, single_launches = 0;
   int64_t created = 0, evicted = 0, ctx_bytes = 0;
   // worker thread only
   std::vector<std::unique_ptr<Context>> ctx;
@@ -179,7 +183,7 @@ bool admit(bfs_server* s, int64_t bytes) {
 
 void drop_context(bfs_server* s, size_t i) {
   Context& c = *s->ctx[i];
-  bfs_batch_free(c.b);
+  if (c.b) bfs_batch_free(c.b);
   if (c.stream) cudaStreamDestroy(c.stream);
   if (c.hdr) cudaFreeHost(c.hdr);
   {
@@ -189,12 +193,37 @@ void drop_context(bfs_server* s, size_t i) {
   s->ctx.erase(s->ctx.begin() + (std::ptrdiff_t)i);
 }
 
-// An idle context of graph gid, a new one, or null (the graph's queries wait).
+Context* new_context(bfs_server* s, int gid) {
+  std::unique_ptr<Context> c(new (std::nothrow) Context());
+  if (!c) return nullptr;
+  c->srv = s;
+  c->gid = gid;
+  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hdr, sizeof(RunHeader)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->stream) cudaStreamDestroy(c->stream);
+    return nullptr;
+  }
+  std::memset(c->hdr, 0, sizeof(RunHeader));
+  s->ctx.push_back(std::move(c));
+  return s->ctx.back().get();
+}
+
+// The graph's single-source context if it is idle (made on first use), else null.
+Context* acquire_single(bfs_server* s, int gid) {
+  for (auto& cp : s->ctx)
+    if (cp->gid == gid && cp->single) return cp->busy ? nullptr : cp.get();
+  Context* c = new_context(s, gid);
+  if (c) c->single = true;
+  return c;
+}
+
+// An idle batch context of graph gid, a new one, or null (the graph's queries wait).
 Context* acquire_context(bfs_server* s, int gid, const bfs_graph* g) {
   int count = 0;
   Context* idle = nullptr;
   for (auto& cp : s->ctx)
-    if (cp->gid == gid) {
+    if (cp->gid == gid && !cp->single) {
       ++count;
       if (!cp->busy && (!idle || cp->last_used > idle->last_used)) idle = cp.get();
     }
@@ -206,7 +235,7 @@ Context* acquire_context(bfs_server* s, int gid, const bfs_graph* g) {
     size_t victim = s->ctx.size();
     for (size_t i = 0; i < s->ctx.size(); ++i) {
       const Context& c = *s->ctx[i];
-      if (c.busy || c.gid == gid) continue;
+      if (c.busy || c.gid == gid || c.single) continue;
       if (victim == s->ctx.size() || c.last_used < s->ctx[victim]->last_used) victim = i;
     }
     if (victim == s->ctx.size()) return nullptr;
@@ -214,27 +243,19 @@ Context* acquire_context(bfs_server* s, int gid, const bfs_graph* g) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->evicted += 1;
   }
-  std::unique_ptr<Context> c(new (std::nothrow) Context());
-  if (!c) return nullptr;
-  c->srv = s;
-  c->gid = gid;
-  if (bfs_batch_create(g, s->opt.with_parents, s->slice, &c->b) != BFS_OK) return nullptr;
-  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost((void**)&c->hdr, sizeof(RunHeader)) != cudaSuccess) {
-    cudaGetLastError();
-    bfs_batch_free(c->b);
-    if (c->stream) cudaStreamDestroy(c->stream);
+  bfs_batch* b = nullptr;
+  if (bfs_batch_create(g, s->opt.with_parents, s->slice, &b) != BFS_OK) return nullptr;
+  Context* c = new_context(s, gid);
+  if (!c) {
+    bfs_batch_free(b);
     return nullptr;
   }
-  std::memset(c->hdr, 0, sizeof(RunHeader));
-  c->bytes = bfs_batch_device_bytes(c->b);
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->ctx_bytes += c->bytes;
-    s->created += 1;
-  }
-  s->ctx.push_back(std::move(c));
-  return s->ctx.back().get();
+  c->b = b;
+  c->bytes = bfs_batch_device_bytes(b);
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->ctx_bytes += c->bytes;
+  s->created += 1;
+  return c;
 }
 
 void launch(bfs_server* s, Context& c) {
@@ -250,7 +271,22 @@ void launch(bfs_server* s, Context& c) {
   c.busy = true;
   c.t_done.store(0, std::memory_order_relaxed);
   c.t_launch = now_ns();
-  int rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch);
+  int rc;
+  if (c.single) {
+    bfs_graph* g;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      g = s->graphs[c.gid].g;
+    }
+    rc = bfsgb::launch_run(g, src[0], nullptr, s->opt.with_parents ? pl[0] : nullptr, c.stream, s->slice, dl[0]);
+    c.epoch = g->epoch & 0x0FFFFFFFu;
+    if (rc == BFS_OK) {
+      const cudaError_t e = cudaMemcpyAsync(c.hdr, g->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, c.stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "copy run header");
+    }
+  } else {
+    rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch);
+  }
   if (rc == BFS_OK) {
     const cudaError_t e = cudaLaunchHostFunc(c.stream, on_launch_done, &c);
     if (e == cudaSuccess) return;
@@ -277,17 +313,21 @@ void schedule(bfs_server* s) {
     Context* c = nullptr;
     for (int gid : order) {
       const bfs_graph* g;
+      size_t waiting;
       {
         std::lock_guard<std::mutex> lk(s->mu);
         g = s->graphs[gid].g;
+        waiting = s->graphs[gid].waiting.size();
       }
+      if (waiting == 1 && s->opt.single_path && (c = acquire_single(s, gid))) break;
       if ((c = acquire_context(s, gid, g))) break;
     }
     if (!c) return;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       std::deque<Query>& w = s->graphs[c->gid].waiting;
-      while (!w.empty() && (int)c->q.size() < s->opt.max_lanes) {
+      const int cap = c->single ? 1 : s->opt.max_lanes;
+      while (!w.empty() && (int)c->q.size() < cap) {
         c->q.push_back(w.front());
         w.pop_front();
       }
@@ -295,6 +335,7 @@ void schedule(bfs_server* s) {
       s->in_flight += 1;
       s->launches += 1;
       s->lanes += (int64_t)c->q.size();
+      if (c->single) s->single_launches += 1;
     }
     launch(s, *c);
   }
@@ -322,6 +363,7 @@ extern "C" void bfs_server_options_default(bfs_server_options* opt) {
   opt->max_lanes = kMaxLanes;
   opt->with_parents = 1;
   opt->contexts_per_graph = 2;
+  opt->single_path = 1;
 }
 
 extern "C" int64_t bfs_server_now_ns(void) { return now_ns(); }
@@ -340,6 +382,7 @@ extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out
   if (o.contexts_per_graph < 1 || o.contexts_per_graph > o.max_concurrent)
     return fail(BFS_ERR_INVALID, "contexts_per_graph must be 1..max_concurrent");
   if (o.with_parents != 0 && o.with_parents != 1) return fail(BFS_ERR_INVALID, "with_parents must be 0 or 1");
+  if (o.single_path != 0 && o.single_path != 1) return fail(BFS_ERR_INVALID, "single_path must be 0 or 1");
   if (o.hbm_reserve_bytes < 0 || o.hbm_budget_bytes < 0) return fail(BFS_ERR_INVALID, "byte limits must be >= 0");
   int dev = 0, cap = 0;
   const cudaError_t e = cudaGetDevice(&dev);
@@ -363,7 +406,7 @@ extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out
   return BFS_OK;
 }
 
-extern "C" int bfs_server_add_graph(bfs_server* s, const bfs_graph* g, int32_t* graph_id) {
+extern "C" int bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id) {
   if (!s || !g || !graph_id) return fail(BFS_ERR_INVALID, "server, graph or graph_id is NULL");
   if (g->device != s->device) return fail(BFS_ERR_INVALID, "the graph lives on another device than the server");
   std::lock_guard<std::mutex> lk(s->mu);
@@ -425,6 +468,7 @@ extern "C" int bfs_server_get_stats(bfs_server* s, bfs_server_stats* st) {
   st->failed = s->failed;
   st->launches = s->launches;
   st->lanes_launched = s->lanes;
+  st->single_launches = s->single_launches;
   st->contexts_created = s->created;
   st->contexts_evicted = s->evicted;
   st->context_bytes = s->ctx_bytes;

@@ -120,7 +120,7 @@ def test_budget_admission_evicts_idle_contexts():
         sizes.append(b.device_bytes)
         b.close()
     budget = max(sizes) + min(sizes) // 2
-    srv = bfs.Server(max_concurrent=1, hbm_budget_bytes=budget)
+    srv = bfs.Server(max_concurrent=1, hbm_budget_bytes=budget, single_path=False)
     ogs = [oracle.Graph(n, s, d) for n, s, d, _ in specs]
     for g in gs:
         srv.add_graph(g)
@@ -180,4 +180,34 @@ def test_open_loop_arrivals_latency_records():
     _check_oracle(ogs, q, recs)
     lat = np.array([r["t_done_ns"] - r["t_arrival_ns"] for r in recs])
     assert (lat > 0).all()
+    srv.close()
+
+
+@pytest.mark.parametrize("single_path", [True, False])
+def test_lone_queries_and_depth_overflow(single_path):
+    """A query that waits alone runs the single-source level loop (uint8 depth,
+    same result as the batch form); a depth past 254 is BFS_ERR_OVERFLOW on
+    either path, and the server stays usable."""
+    bfs, srv, gs, ogs = _setup(max_concurrent=2, single_path=single_path)
+    q = _queries(gs, 30, seed=41)
+    recs = []
+    for gid, s in q:
+        srv.submit(gid, s)
+        recs += srv.drain()
+    _check_oracle(ogs, q, recs)
+    st = srv.stats()
+    assert st["single_launches"] == (30 if single_path else 0)
+    e = np.array([(i, i + 1) for i in range(299)], np.int32)  # depth 299 from an end
+    deep = gpu_graph(300, e[:, 0], e[:, 1], th=8)
+    gid = srv.add_graph(deep)
+    srv.submit(gid, 0)
+    (r,) = srv.drain()
+    assert r["status"] == bfs.BFS_ERR_OVERFLOW
+    srv.submit(gid, 150)  # depths <= 150
+    (r,) = srv.drain()
+    assert r["status"] == 0
+    og = oracle.Graph(300, e[:, 0], e[:, 1])
+    want_d, want_p = og.bfs_batch_u8([150])
+    assert_same(r["depth"].cpu().numpy(), want_d[0], "depth after an overflow")
+    assert_same(r["parent"].cpu().numpy(), want_p[0], "parent after an overflow")
     srv.close()
