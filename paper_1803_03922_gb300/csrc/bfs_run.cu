@@ -561,107 +561,112 @@ __device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
 // ---- bitmap -> frontier queues --------------------------------------------------------------
 
 // Reads the discovered bitmap Nsrc of a level and writes the next frontier as a
-// normal-vertex queue Q and a delegate chunk list CL.  The bitmap is cut into
-// tiles of one word per thread; a CTA scans its tile's bit counts, reserves the
-// tile's queue range with one atomic, then handles the tile's new vertices one
-// per thread (k-th set bit -> word by binary search over the prefix, bit by
-// rank).  With `merge`, also ORs Nsrc into V and clears Nclr.  With `count`
-// (after a forward level), also writes depth `depth` for every new vertex and
-// adds n_f and m_f.  Called by all threads.
+// normal-vertex queue Q and a delegate chunk list CL.  Each warp takes items of
+// 32 bitmap words (1024 vertices; 2 words in the delegate prefix, which is dense
+// in new vertices), so no item is long: lane i loads word i, a warp scan of the bit counts gives every set bit a
+// rank, the warp reserves its queue and chunk ranges with one atomic each, and
+// then handles the item's new vertices 32 at a time (rank -> word by a binary
+// search over the lanes' prefixes, bit by rank within the word).  With `merge`,
+// also ORs Nsrc into V and clears Nclr.  With `count` (after a forward level),
+// also writes depth `depth` for every new vertex and adds n_f and m_f.
 __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
                                      int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* slot, bool merge,
                                      bool count, int depth, Acc& acc) {
-  __shared__ unsigned s_nb[kThreads];
-  __shared__ int s_wpre[kThreads];
-  __shared__ int s_npre[kThreads];
-  __shared__ unsigned long long s_base[2];
   const int64_t W = p.words;
-  const int tid = threadIdx.x;
-  for (int64_t t0 = (int64_t)blockIdx.x * kThreads; t0 < W; t0 += (int64_t)gridDim.x * kThreads) {
-    const int64_t w = t0 + tid;
+  const int lane = lane_id();
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // the delegate prefix is dense in new vertices after a forward level: items of
+  // two words there, 32 words elsewhere
+  constexpr int kDelWords = 2;
+  const int64_t Wd = min(W, ((int64_t)p.d + 31) / 32);
+  const int64_t nd_items = (Wd + kDelWords - 1) / kDelWords;
+  const int64_t Wd2 = min(W, nd_items * kDelWords);
+  const int64_t nitems = nd_items + (W - Wd2 + 31) / 32;
+  for (int64_t it = gwarp; it < nitems; it += nwarps) {
+    const bool del_item = it < nd_items;
+    const int64_t wb = del_item ? it * kDelWords : Wd2 + (it - nd_items) * 32;
+    const int nw = del_item ? kDelWords : 32;
+    const int64_t w = wb + lane;
     unsigned nb = 0;
-    if (w < W) {
+    if (lane < nw && w < W) {
       nb = __ldcg(Nsrc + w);
       if (merge) {
         if (nb) p.V[w] |= nb;
         Nclr[w] = 0u;
       }
     }
-    if (!__syncthreads_or(nb != 0)) continue;
+    if (!__any_sync(kFull, nb != 0)) continue;
     const int64_t v0 = w * 32;
-    unsigned dmask = 0;
+    unsigned dmask = 0;  // delegate bits of this lane's word
     if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
-    unsigned long long ea, eb, T, Tn;
-    block_scan2((unsigned long long)__popc(nb), (unsigned long long)__popc(nb & ~dmask), ea, eb, T, Tn);
-    s_nb[tid] = nb;
-    s_wpre[tid] = (int)ea;
-    s_npre[tid] = (int)eb;
-    if (tid == 0) s_base[0] = Tn ? atomicAdd(&slot->qn, Tn) : 0ull;
-    __syncthreads();
-    const unsigned long long qbase = s_base[0];
-    const bool has_del = t0 * 32 < p.d;
-    unsigned long long nch_local = 0;
-    // four new vertices per thread and step, so their degree loads overlap
-    for (int k0 = tid; k0 < (int)T; k0 += 4 * kThreads) {
-      int vv[4], jj[4], bb[4];
+    const int cnt = __popc(nb), ncnt = __popc(nb & ~dmask);
+    int incl = cnt, nincl = ncnt;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int k = k0 + u * kThreads;
-        int j = 0;
-        if (k < (int)T) {
-#pragma unroll
-          for (int st = kThreads / 2; st >= 1; st >>= 1)
-            if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
-          bb[u] = nth_set_bit(s_nb[j], k - s_wpre[j]);
-          vv[u] = (int)((t0 + j) * 32 + bb[u]);
-        } else {
-          bb[u] = 0;
-          vv[u] = -1;
-        }
-        jj[u] = j;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int a = __shfl_up_sync(kFull, incl, o), b = __shfl_up_sync(kFull, nincl, o);
+      if (lane >= o) {
+        incl += a;
+        nincl += b;
       }
-      int dg[4];
+    }
+    const int T = __shfl_sync(kFull, incl, 31), Tn = __shfl_sync(kFull, nincl, 31);
+    const int excl = incl - cnt, nexcl = nincl - ncnt;
+    unsigned long long qbase = 0;
+    if (lane == 0 && Tn) qbase = atomicAdd(&slot->qn, (unsigned long long)Tn);
+    qbase = __shfl_sync(kFull, qbase, 0);
+    for (int k0 = 0; k0 < T; k0 += 32) {
+      const int k = k0 + lane;
+      const bool act = k < T;
+      int j = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) dg[u] = vv[u] >= 0 ? p.deg[vv[u]] : 0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int v = vv[u];
-        if (v < 0) continue;
-        const int64_t deg = dg[u];
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int t = __shfl_sync(kFull, incl, j + sh - 1);
+        if (t <= k) j += sh;
+      }
+      const unsigned m = __shfl_sync(kFull, nb, j);
+      const unsigned dm = __shfl_sync(kFull, dmask, j);
+      const int ex = __shfl_sync(kFull, excl, j), nex = __shfl_sync(kFull, nexcl, j);
+      const int bit = act ? nth_set_bit(m, k - ex) : 0;
+      const int v = (int)((wb + j) * 32 + bit);
+      const int dg = act ? p.deg[v] : 0;
+      unsigned long long nc = 0;
+      if (act) {
         if (count) {
           p.depth_i[v] = depth;
           acc.nf += 1;
-          acc.mf += (unsigned long long)deg;
+          acc.mf += (unsigned long long)dg;
         }
-        if (v >= p.d) {
-          const int j = jj[u];
-          const int64_t jv0 = (t0 + j) * 32;
-          unsigned jd = 0;
-          if (jv0 < p.d) jd = (p.d - jv0 >= 32) ? kFull : ((1u << (p.d - jv0)) - 1u);
-          Q[qbase + s_npre[j] + __popc(s_nb[j] & ~jd & ((1u << bb[u]) - 1u))] = v;
-        } else {
-          nch_local += (unsigned long long)((deg + kChunk - 1) / kChunk);
-        }
+        if (v >= p.d)
+          Q[qbase + nex + __popc(m & ~dm & ((1u << bit) - 1u))] = v;
+        else
+          nc = ((unsigned long long)dg + kChunk - 1) / kChunk;
       }
-    }
-    if (has_del) {
-      unsigned long long ec, dummy, tc, dummy2;
-      block_scan2(nch_local, 0ull, ec, dummy, tc, dummy2);
-      if (tid == 0) s_base[1] = tc ? atomicAdd(&slot->nch, tc) : 0ull;
-      __syncthreads();
-      unsigned long long cb = s_base[1] + ec;
-      for (int k = tid; k < (int)T; k += kThreads) {
-        int j = 0;
+      if (__any_sync(kFull, nc != 0)) {  // delegates: their row chunks, 32 entries per step
+        long long ci = (long long)nc;
 #pragma unroll
-        for (int st = kThreads / 2; st >= 1; st >>= 1)
-          if (j + st < kThreads && s_wpre[j + st] <= k) j += st;
-        const int v = (int)((t0 + j) * 32 + nth_set_bit(s_nb[j], k - s_wpre[j]));
-        if (v >= p.d) continue;
-        const int64_t nc = ((int64_t)p.deg[v] + kChunk - 1) / kChunk;
-        for (int64_t c = 0; c < nc; ++c) CL[cb++] = make_int2(v, (int)c);
+        for (int o = 1; o < 32; o <<= 1) {
+          const long long t = __shfl_up_sync(kFull, ci, o);
+          if (lane >= o) ci += t;
+        }
+        const long long C = __shfl_sync(kFull, ci, 31);
+        unsigned long long cbase = 0;
+        if (lane == 0) cbase = atomicAdd(&slot->nch, (unsigned long long)C);
+        cbase = __shfl_sync(kFull, cbase, 0);
+        for (long long e0 = 0; e0 < C; e0 += 32) {
+          const long long e = e0 + lane;
+          int o = 0;
+#pragma unroll
+          for (int sh = 16; sh >= 1; sh >>= 1) {
+            const long long t = __shfl_sync(kFull, ci, o + sh - 1);
+            if (t <= e) o += sh;
+          }
+          const int ov = __shfl_sync(kFull, v, o);
+          const long long oex = __shfl_sync(kFull, ci, o) - (long long)__shfl_sync(kFull, nc, o);
+          if (e < C) CL[cbase + e] = make_int2(ov, (int)(e - oex));
+        }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -769,7 +774,7 @@ __device__ __forceinline__ int iw_code(long long unvisited, int n_ni) {
 __device__ void run_body(const BfsParams& p) {
   // state of the direction decision, kept by CTA 0 (the barriers' master)
   __shared__ long long s_mu, s_unv;
-  __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te, s_tnf;
+  __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te, s_tnf, s_log[5];
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
@@ -889,7 +894,16 @@ __device__ void run_body(const BfsParams& p) {
       flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
       if (grid_sync(p, seq, no_master) < 0) return;
     }
-    if (leader) s_te = gtimer();
+    if (leader) {
+      s_te = gtimer();
+      // this level's counters for its log, final by now (loaded ahead of the
+      // decision barrier so the log costs no round trip after it)
+      s_log[0] = __ldcg(&sc->n_f);
+      s_log[1] = __ldcg(&sc->m_f);
+      s_log[2] = __ldcg(&sc->scanned);
+      s_log[3] = __ldcg(&sc->edges);
+      s_log[4] = __ldcg(&sc->qn);
+    }
     if (dir == 0) {
       // merge, then the next frontier's queues, depths and counts
       frontier_from_bitmap(p, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true, true, L + 1,
@@ -925,13 +939,13 @@ __device__ void run_body(const BfsParams& p) {
       lg.t_end = gtimer();
       lg.dir = dir;
       lg.converted = conv ? 1 : 0;
-      lg.n_f = __ldcg(&sc->n_f);
-      lg.m_f = __ldcg(&sc->m_f);
-      lg.scanned = __ldcg(&sc->scanned);
-      lg.edges = dir == 0 ? __ldcg(&sc->m_f) : __ldcg(&sc->edges);
-      lg.fix_edges = __ldcg(&sc->fix_edges);
+      lg.n_f = s_log[0];
+      lg.m_f = s_log[1];
+      lg.scanned = s_log[2];
+      lg.edges = dir == 0 ? s_log[1] : s_log[3];
+      lg.fix_edges = p.td_parent == BFS_TD_PARENT_PULL ? __ldcg(&sc->fix_edges) : 0ull;
       lg.found = s_tnf;
-      lg.qn = __ldcg(&sc->qn);
+      lg.qn = s_log[4];
       lg.t_begin = s_tb;
       lg.t_expand = s_te;
       lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
