@@ -75,6 +75,7 @@ int alloc_run_state(bfs_graph* g) {
   int rc;
   cudaError_t e;
   if ((rc = dmalloc(&g->V, words, &t, "alloc V"))) return rc;
+  if ((rc = dmalloc(&g->V1, words, &t, "alloc V1"))) return rc;
   if ((rc = dmalloc(&g->N0, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->N1, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->depth_i, (size_t)g->n_ni + 1, &t, "alloc depth"))) return rc;
@@ -98,7 +99,7 @@ int alloc_run_state(bfs_graph* g) {
 }
 
 void free_all(bfs_graph* g) {
-  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->V, g->N0, g->N1, g->depth_i,
+  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->V, g->V1, g->N0, g->N1, g->depth_i,
                   g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);

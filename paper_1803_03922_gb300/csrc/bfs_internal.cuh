@@ -63,7 +63,8 @@ struct BfsParams {
   const int32_t* internal_of;// [n]
   const int4* head;          // [2 n_ni]: first kHead neighbours (internal ids, -1 pad), then their caller ids
   const int32_t* deg;        // [n_ni] degree
-  uint32_t* V;               // visited bitmap, [words]
+  uint32_t* V;               // visited bitmaps, [words] each: level L reads one and writes
+  uint32_t* V1;              // the other (depth <= L and depth <= L+1)
   uint32_t* N0;              // discovered-this-level bitmaps, [words] each
   uint32_t* N1;
   int32_t* depth_i;          // [n_ni]
@@ -117,6 +118,7 @@ struct bfs_graph {
   int32_t* deg = nullptr;
   // run state
   uint32_t* V = nullptr;
+  uint32_t* V1 = nullptr;
   uint32_t* N0 = nullptr;
   uint32_t* N1 = nullptr;
   int32_t* depth_i = nullptr;

@@ -54,15 +54,13 @@ __device__ void flush_block(Acc& a, unsigned long long* nf, unsigned long long* 
   a = Acc();
 }
 
-// Visited-state probe for the pull scans.  Backward: visited before this level
-// (V is read-only during the expansion).  Parent pick after a forward level:
-// visited and not discovered in this level (V is being merged concurrently; the
-// second test makes the answer the same either way).
+// Visited-state probe for the pull scans, against the level's visited bitmap Vc
+// (vertices at depth <= L; read-only during level L, whose discoveries go to the
+// other buffer).  For an unvisited vertex (backward) or one found in level L
+// (parent pick after a forward level) a neighbour in Vc is at depth L exactly.
 template <bool kFix>
-__device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t* __restrict__ Ncur) {
-  bool s = (p.V[c >> 5] >> (c & 31)) & 1u;
-  if (kFix && s) s = !((__ldcg(Ncur + (c >> 5)) >> (c & 31)) & 1u);
-  return s;
+__device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t* __restrict__ Vc) {
+  return (Vc[c >> 5] >> (c & 31)) & 1u;
 }
 
 // Whole-warp scan of row entries [from, end) of a row starting at rbeg, 128
@@ -271,20 +269,22 @@ __device__ int pull_head(const BfsParams& p, bool act, int v, const uint32_t* __
 // gets its bit in N (fire-and-forget atomicOr); with atomicMin parents, the
 // frontier vertex's caller id is also offered to v's parent slot.  Which lane
 // set the bit does not matter: the level end builds the next frontier from N.
-__device__ __forceinline__ void td_edge(const BfsParams& p, int v, int pcaller, uint32_t* __restrict__ N) {
+__device__ __forceinline__ void td_edge(const BfsParams& p, const uint32_t* __restrict__ Vc, int v, int pcaller,
+                                        uint32_t* __restrict__ N) {
   if (v < 0) return;
   const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
-  if (p.V[w] & bit) return;
+  if (Vc[w] & bit) return;
   if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
   if (!(p.tuning & 1) || !(__ldcg(N + w) & bit)) atomicOr(N + w, bit);
 }
 
 // Four row entries of one lane: the four visited-bit probes are issued before
 // any reduction, so they are in flight together.
-__device__ __forceinline__ void td_edge4(const BfsParams& p, const int (&v)[4], int pcaller, uint32_t* __restrict__ N) {
+__device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __restrict__ Vc, const int (&v)[4],
+                                         int pcaller, uint32_t* __restrict__ N) {
   unsigned vw[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? p.V[(unsigned)v[t] >> 5] : kFull;
+  for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? Vc[(unsigned)v[t] >> 5] : kFull;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
@@ -298,8 +298,8 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const int (&v)[4], 
 // 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
 // concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
 // whose inclusive degree prefix first exceeds e).
-__device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int64_t qn, int64_t b,
-                         uint32_t* __restrict__ N) {
+__device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, const int32_t* __restrict__ Qc,
+                         int64_t qn, int64_t b, uint32_t* __restrict__ N) {
   const int lane = lane_id();
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
@@ -324,12 +324,12 @@ __device__ void td_batch(const BfsParams& p, const int32_t* __restrict__ Qc, int
     const int64_t ob = __shfl_sync(kFull, beg, pos);
     const int64_t ox = __shfl_sync(kFull, excl, pos);
     const int opc = __shfl_sync(kFull, pc, pos);
-    td_edge(p, e < total ? p.col[ob + (e - ox)] : -1, opc, N);
+    td_edge(p, Vc, e < total ? p.col[ob + (e - ox)] : -1, opc, N);
   }
 }
 
 // One kChunk-entry piece of a delegate's row, 128-bit loads.
-__device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) {
+__device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, int2 ck, uint32_t* __restrict__ N) {
   const int lane = lane_id();
   const int u = ck.x;
   const int64_t rb = p.off[u], re = p.off[u + 1];
@@ -345,11 +345,11 @@ __device__ void td_chunk(const BfsParams& p, int2 ck, uint32_t* __restrict__ N) 
     if (ja < end) {
       const int v[4] = {ja >= beg ? ca.x : -1, (ja + 1 >= beg && ja + 1 < end) ? ca.y : -1,
                         (ja + 2 >= beg && ja + 2 < end) ? ca.z : -1, (ja + 3 >= beg && ja + 3 < end) ? ca.w : -1};
-      td_edge4(p, v, pc, N);
+      td_edge4(p, Vc, v, pc, N);
     }
     if (jb < end) {
       const int v[4] = {cb.x, jb + 1 < end ? cb.y : -1, jb + 2 < end ? cb.z : -1, jb + 3 < end ? cb.w : -1};
-      td_edge4(p, v, pc, N);
+      td_edge4(p, Vc, v, pc, N);
     }
   }
 }
@@ -381,7 +381,7 @@ struct WorkCursor {
 // Work items of a forward level: the delegate chunks of F_L, then the normal
 // queue in batches of 32; warp w takes items w, w + warps, ... (a shared counter
 // measured slower here: the chunks are uniform).
-__device__ void expand_td(const BfsParams& p, int L) {
+__device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, int L) {
   const LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sc->qn);
   const int64_t nch = (int64_t)__ldcg(&sc->nch);
@@ -393,9 +393,9 @@ __device__ void expand_td(const BfsParams& p, int L) {
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = gwarp; it < total; it += nwarps) {
     if (it < nch)
-      td_chunk(p, CLc[it], N);
+      td_chunk(p, Vc, CLc[it], N);
     else
-      td_batch(p, Qc, qn, it - nch, N);
+      td_batch(p, Vc, Qc, qn, it - nch, N);
   }
 }
 
@@ -422,16 +422,18 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // per step.  A vertex that finds its parent gets depth and parent; its bit is
 // collected in the warp's shared copy of the item's words (the warp owns them)
 // and each word is written to N once.
-__device__ bool bu_item(const BfsParams& p, int L, int64_t w0, int iw, unsigned* found, uint32_t* __restrict__ N,
-                        LevelSlot* sc, Acc& acc) {
+__device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
+                        uint32_t* __restrict__ Nclr, int L, int64_t w0, int iw, unsigned* found,
+                        uint32_t* __restrict__ N, LevelSlot* sc, Acc& acc) {
   bool deferred = false;
   const int lane = lane_id();
   const int64_t W = p.words;
   const int tail = p.n_ni & 31;
   const int64_t w = w0 + lane;
-  unsigned vis = kFull;
+  unsigned vis = kFull, vraw = 0;
   if (lane < iw && w < W) {
-    vis = p.V[w];
+    vraw = Vc[w];
+    vis = vraw;
     if (w == W - 1 && tail) vis |= ~((1u << tail) - 1u);
   }
   const unsigned unv = ~vis;
@@ -466,10 +468,10 @@ __device__ bool bu_item(const BfsParams& p, int L, int64_t w0, int iw, unsigned*
     const HeadRec hB = head_load(p, aB, vB);
     int hitA = -1, cidA = -1, hitB = -1, cidB = -1;
     int64_t kA = 0, kB = 0;
-    if (aA) head_probe<false>(p, hA, nullptr, hitA, cidA, kA);
-    if (aB) head_probe<false>(p, hB, nullptr, hitB, cidB, kB);
-    pull_tail<false>(p, aA, vA, hA.deg, nullptr, hitA, cidA, kA, sc);
-    pull_tail<false>(p, aB, vB, hB.deg, nullptr, hitB, cidB, kB, sc);
+    if (aA) head_probe<false>(p, hA, Vc, hitA, cidA, kA);
+    if (aB) head_probe<false>(p, hB, Vc, hitB, cidB, kB);
+    pull_tail<false>(p, aA, vA, hA.deg, Vc, hitA, cidA, kA, sc);
+    pull_tail<false>(p, aB, vB, hB.deg, Vc, hitB, cidB, kB, sc);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       deferred |= (q ? aB : aA) && (q ? hitB : hitA) == kDeferred;
@@ -494,12 +496,15 @@ __device__ bool bu_item(const BfsParams& p, int L, int64_t w0, int iw, unsigned*
     }
     __syncwarp();
   }
-  if (lane < iw) {
+  // the warp owns its words: found bits, the next visited bitmap, and the other
+  // discovered bitmap cleared for the level after (deferred rows add their bits
+  // after the next grid barrier)
+  if (lane < iw && w < W) {
     const unsigned f = found[lane];
-    if (f) {
-      atomicOr(N + w0 + lane, f);  // deferred rows of other warps may add bits to this word
-      found[lane] = 0u;
-    }
+    N[w] = f;
+    Vn[w] = vraw | f;
+    Nclr[w] = 0u;
+    found[lane] = 0u;
   }
   __syncwarp();
   return deferred;
@@ -510,7 +515,8 @@ __device__ bool bu_item(const BfsParams& p, int L, int64_t w0, int iw, unsigned*
 // kShort entries are deferred to the level's long-row list, which all warps then
 // drain with dynamic hand-out, one row per warp and 128-bit loads, so that long
 // scans spread over the grid instead of stalling the warp that met them.
-__device__ bool expand_bu(const BfsParams& p, int L, int iw, Acc& acc) {
+__device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
+                          uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc) {
   __shared__ unsigned s_found[kWarpsPerBlock][32];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
@@ -523,7 +529,8 @@ __device__ bool expand_bu(const BfsParams& p, int L, int iw, Acc& acc) {
   LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t nitems = (W + iw - 1) / iw;
   bool deferred = false;
-  for (int64_t it = gwarp; it < nitems; it += nwarps) deferred |= bu_item(p, L, it * iw, iw, found, N, sc, acc);
+  for (int64_t it = gwarp; it < nitems; it += nwarps)
+    deferred |= bu_item(p, Vc, Vn, Nclr, L, it * iw, iw, found, N, sc, acc);
   return deferred;
 }
 
@@ -531,7 +538,8 @@ __device__ bool expand_bu(const BfsParams& p, int L, int iw, Acc& acc) {
 // list is complete and V is still read-only): all warps take deferred rows from
 // a shared counter in runs and scan them with 128-bit loads; a vertex found here
 // sets its bit in N with an atomic.
-__device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
+__device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn, int L,
+                                Acc& acc) {
   LevelSlot* sc = p.slot + (L & (kSlots - 1));
   uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
   const long long nl = (long long)__ldcg(&sc->nlong);
@@ -543,7 +551,7 @@ __device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
     const int v = p.longq[e];
     const int64_t rb = p.off[v], re = rb + p.deg[v];
     int64_t kv;
-    const int hit = warp_scan<false>(p, rb, rb + kHead, re, nullptr, kv);
+    const int hit = warp_scan<false>(p, rb, rb + kHead, re, Vc, kv);
     if (lane_id() == 0) {
       acc.scanned += 1;
       acc.edges += (unsigned long long)kv;
@@ -551,6 +559,7 @@ __device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
         p.parent_i[v] = p.caller_of[hit];
         p.depth_i[v] = L + 1;
         atomicOr(Ncur + (v >> 5), 1u << (v & 31));
+        atomicOr(Vn + (v >> 5), 1u << (v & 31));
         acc.nf += 1;
         acc.mf += (unsigned long long)(re - rb);
       }
@@ -567,9 +576,10 @@ __device__ void drain_long_rows(const BfsParams& p, int L, Acc& acc) {
 // rank, the warp reserves its queue and chunk ranges with one atomic each, and
 // then handles the item's new vertices 32 at a time (rank -> word by a binary
 // search over the lanes' prefixes, bit by rank within the word).  With `merge`,
-// also ORs Nsrc into V and clears Nclr.  With `count` (after a forward level),
+// also writes the next visited bitmap Vn = Vc | Nsrc and clears Nclr.  With `count` (after a forward level),
 // also writes depth `depth` for every new vertex and adds n_f and m_f.
-__device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
+__device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
+                                     const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
                                      int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* slot, bool merge,
                                      bool count, int depth, Acc& acc) {
   const int64_t W = p.words;
@@ -592,7 +602,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
     if (lane < nw && w < W) {
       nb = __ldcg(Nsrc + w);
       if (merge) {
-        if (nb) p.V[w] |= nb;
+        Vn[w] = Vc[w] | nb;
         Nclr[w] = 0u;
       }
     }
@@ -670,28 +680,9 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
   }
 }
 
-// V |= Ncur and Nclr = 0, 4 words per thread (the level end of a backward level).
-__device__ void merge_bitmaps(const BfsParams& p, const uint32_t* __restrict__ Ncur, uint32_t* __restrict__ Nclr) {
-  const int64_t W4 = (p.words + 3) / 4;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < W4; q += stride) {
-    const uint4 nb4 = __ldcg(reinterpret_cast<const uint4*>(Ncur) + q);
-    if (nb4.x | nb4.y | nb4.z | nb4.w) {
-      uint4 v4 = reinterpret_cast<uint4*>(p.V)[q];
-      v4.x |= nb4.x;
-      v4.y |= nb4.y;
-      v4.z |= nb4.z;
-      v4.w |= nb4.w;
-      reinterpret_cast<uint4*>(p.V)[q] = v4;
-    }
-    reinterpret_cast<uint4*>(Nclr)[q] = make_uint4(0, 0, 0, 0);
-  }
-}
-
 // Canonical parents of the vertices found by a forward level, by a first-hit
 // scan of their sorted rows (the PULL option).
-__device__ void pull_parents(const BfsParams& p, int L, Acc& acc) {
-  uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+__device__ void pull_parents(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, Acc& acc) {
   const LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sn->qn);
   const int64_t nch = (int64_t)__ldcg(&sn->nch);
@@ -706,7 +697,7 @@ __device__ void pull_parents(const BfsParams& p, int L, Acc& acc) {
     const int v = act ? Qn[i] : 0;
     int64_t kv = 0;
     int cid = -1, deg = 0;
-    const int hit = pull_head<true>(p, act, v, Ncur, kv, cid, deg);
+    const int hit = pull_head<true>(p, act, v, Vc, kv, cid, deg);
     if (act) {
       acc.fix += (unsigned long long)kv;
       if (hit >= 0) p.parent_i[v] = cid;
@@ -717,7 +708,7 @@ __device__ void pull_parents(const BfsParams& p, int L, Acc& acc) {
     if (ck.y != 0) continue;
     const int64_t rb = p.off[ck.x], re = p.off[ck.x + 1];
     int64_t kv;
-    const int hit = warp_scan<true>(p, rb, rb, re, Ncur, kv);
+    const int hit = warp_scan<true>(p, rb, rb, re, Vc, kv);
     if (lane == 0) {
       acc.fix += (unsigned long long)kv;
       if (hit >= 0) p.parent_i[ck.x] = p.caller_of[hit];
@@ -750,6 +741,16 @@ __device__ int decide(const BfsParams& p, int L1, int cur, unsigned long long nf
       const bool small = nf * (unsigned long long)p.beta < (unsigned long long)p.n;
       return (small && nf < prev_nf) ? 0 : 1;
     }
+  }
+}
+
+// Spread of the CTAs' finishing times of an expansion (the tracing option).
+__device__ void trace_done(LevelSlot* sc) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t = gtimer();
+    atomicMin(&sc->t_first, t);
+    atomicMax(&sc->t_last, t);
   }
 }
 
@@ -853,6 +854,7 @@ __device__ void run_body(const BfsParams& p) {
   const unsigned long long t_start = gtimer();
   if (leader) p.hdr->t_init = t_start;
   int L = 0;
+  int vpar = 0;  // visited bitmap of the current level: V (0) or V1 (1)
   while (!(bits & kBitDone)) {
     // Bounds against a run that does not end: at most n_ni+1 levels, and the
     // run's deadline.  A failure set here ends every CTA at its next barrier.
@@ -865,64 +867,24 @@ __device__ void run_body(const BfsParams& p) {
     LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
     uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
     uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
+    const uint32_t* Vc = vpar ? p.V1 : p.V;  // depth <= L, read-only during the level
+    uint32_t* Vn = vpar ? p.V : p.V1;        // depth <= L+1, written during the level
     if (conv) {
       // F_L is the bitmap of the previous (backward) level's discoveries.
-      frontier_from_bitmap(p, Noth, nullptr, (L & 1) ? p.Q1 : p.Q0, (L & 1) ? p.CL1 : p.CL0, sc, false, false, 0,
-                           acc);
+      frontier_from_bitmap(p, Vc, Vn, Noth, nullptr, (L & 1) ? p.Q1 : p.Q0, (L & 1) ? p.CL1 : p.CL0, sc, false, false,
+                           0, acc);
       if (grid_sync(p, seq, no_master) < 0) return;
     }
     if (leader) s_tb = gtimer();
-    bool deferred = false;
-    if (dir == 0) {
-      expand_td(p, L);
-    } else {
-      deferred = expand_bu(p, L, iw, acc);
-      flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
-    }
-    if (trace) {  // spread of the CTAs' finishing times
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        const unsigned long long t = gtimer();
-        atomicMin(&sc->t_first, t);
-        atomicMax(&sc->t_last, t);
-      }
-    }
-    const int eb = grid_sync(p, seq, [&](int fl) { return fl & kBitDrain; }, deferred ? kBitDrain : 0);
-    if (eb < 0) return;
-    if (eb & kBitDrain) {
-      drain_long_rows(p, L, acc);
-      flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
-      if (grid_sync(p, seq, no_master) < 0) return;
-    }
-    if (leader) {
-      s_te = gtimer();
-      // this level's counters for its log, final by now (loaded ahead of the
-      // decision barrier so the log costs no round trip after it)
+    // The barrier master's step once the level's counters are complete: the
+    // direction of level L+1, and this level's log counters (loaded together).
+    auto master = [&](int) {
+      const unsigned long long nf = __ldcg(&sn->n_f), mf = __ldcg(&sn->m_f);
       s_log[0] = __ldcg(&sc->n_f);
       s_log[1] = __ldcg(&sc->m_f);
       s_log[2] = __ldcg(&sc->scanned);
       s_log[3] = __ldcg(&sc->edges);
       s_log[4] = __ldcg(&sc->qn);
-    }
-    if (dir == 0) {
-      // merge, then the next frontier's queues, depths and counts
-      frontier_from_bitmap(p, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true, true, L + 1,
-                           acc);
-      flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
-      if (p.td_parent == BFS_TD_PARENT_PULL) {
-        if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
-        pull_parents(p, L, acc);
-        flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
-      }
-    } else {
-      merge_bitmaps(p, Ncur, Noth);
-    }
-    if (leader) {
-      p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
-      p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
-    }
-    bits = grid_sync(p, seq, [&](int) {
-      const unsigned long long nf = __ldcg(&sn->n_f), mf = __ldcg(&sn->m_f);
       s_tnf = nf;
       s_mu -= (long long)mf;
       s_unv -= (long long)nf;
@@ -932,9 +894,47 @@ __device__ void run_body(const BfsParams& p) {
       const int nd = decide(p, L + 1, dir, nf, mf, s_prev_nf, s_mu, s_unv);
       s_prev_nf = nf;
       return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni);
-    });
+    };
+    if (dir == 0) {
+      expand_td(p, Vc, L);
+      if (trace) trace_done(sc);
+      if (grid_sync(p, seq, no_master) < 0) return;
+      if (leader) s_te = gtimer();
+      // the next frontier's queues, depths and counts; Vn = Vc | N
+      frontier_from_bitmap(p, Vc, Vn, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true, true,
+                           L + 1, acc);
+      flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+      if (p.td_parent == BFS_TD_PARENT_PULL) {
+        if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
+        pull_parents(p, Vc, L, acc);
+        flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+      }
+      if (leader) {
+        p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+        p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
+      }
+      bits = grid_sync(p, seq, master);
+    } else {
+      // backward: the items write N, Vn and the cleared other bitmap themselves,
+      // so one barrier ends the level unless long rows were deferred
+      const bool deferred = expand_bu(p, Vc, Vn, Noth, L, iw, acc);
+      flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
+      if (trace) trace_done(sc);
+      if (leader) {
+        s_te = gtimer();
+        p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+        p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
+      }
+      bits = grid_sync(p, seq, [&](int fl) { return (fl & kBitDrain) ? kBitDrain : master(fl); },
+                       deferred ? kBitDrain : 0);
+      if (bits >= 0 && (bits & kBitDrain)) {
+        drain_long_rows(p, Vc, Vn, L, acc);
+        flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
+        bits = grid_sync(p, seq, master);
+      }
+    }
     if (bits < 0) return;
-    if (leader && L < BFS_LOG_LEVELS) {  // the level's log, after the release (slot L stays intact until L+2)
+    if (leader && L < BFS_LOG_LEVELS) {  // the level's log (slot L stays intact until L+2)
       LevelLogDev& lg = p.log[L];
       lg.t_end = gtimer();
       lg.dir = dir;
@@ -951,11 +951,13 @@ __device__ void run_body(const BfsParams& p) {
       lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
       lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
     }
+    vpar ^= 1;
     ++L;
   }
 
   // ---- results in caller ids: 4 consecutive caller ids per thread ----
   if (leader) p.hdr->t_loop = gtimer();
+  const uint32_t* Vf = vpar ? p.V1 : p.V;
   const int64_t C4 = ((int64_t)p.n + 3) / 4;
   for (int64_t q = gtid; q < C4; q += gthreads) {
     const int4 iv = reinterpret_cast<const int4*>(p.internal_of)[q];
@@ -964,7 +966,7 @@ __device__ void run_body(const BfsParams& p) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int v = vs[t];
-      const bool r = v >= 0 && v < p.n_ni && ((p.V[v >> 5] >> (v & 31)) & 1u);
+      const bool r = v >= 0 && v < p.n_ni && ((Vf[v >> 5] >> (v & 31)) & 1u);
       dv[t] = r ? p.depth_i[v] : -1;
       pv[t] = r ? p.parent_i[v] : -1;
       if (q * 4 + t == p.src_c) {
@@ -1044,6 +1046,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.deg = g->deg;
   p.longq = g->longq;
   p.V = g->V;
+  p.V1 = g->V1;
   p.N0 = g->N0;
   p.N1 = g->N1;
   p.depth_i = g->depth_i;
