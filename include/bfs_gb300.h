@@ -143,7 +143,9 @@ typedef struct bfs_stats {
   int64_t reached;         /* vertices with depth >= 0 */
   int64_t component_edges; /* unique undirected edges in the traversed component (GTEPS numerator) */
   int64_t edges_examined;  /* sum over levels */
-  int64_t model_bytes;     /* algorithmic HBM bytes of this run (byte model of the design notes) */
+  int64_t model_bytes;     /* algorithmic HBM bytes of this run, from the per-level counters: a
+                              column and a probe per examined entry, offsets and queue entries per
+                              frontier vertex, depth/parent/queue per found vertex, bitmap passes */
   uint64_t device_ns;      /* %globaltimer span of the whole run (set-up, levels, results) */
   uint64_t setup_ns;       /* part of device_ns spent clearing state before level 0 */
   uint64_t result_ns;      /* part of device_ns spent writing the caller-indexed results */
@@ -154,7 +156,9 @@ typedef struct bfs_stats {
  * int32 buffers indexed by caller id, both in device memory or both in host
  * memory: depth[v] = hop distance (-1 unreached), parent[v] = canonical parent
  * (parent[source] = source, -1 unreached).  Device buffers: asynchronous on
- * `stream`.  Host buffers: results are copied back and `stream` is synchronized.
+ * `stream`.  Host buffers: `stream` is synchronized; page-locked (pinned) host
+ * buffers are written by the kernel directly, pageable ones through a device
+ * copy.
  * stats (optional, host): filled after synchronizing `stream`.
  * One run at a time per graph: runs on one stream are ordered; runs of the same
  * graph on different streams must not overlap.
@@ -207,7 +211,8 @@ int64_t bfs_batch_device_bytes(const bfs_batch* b);
  * depth[k*n] uint8 row-major by query (255 = unreached); parent[k*n] int32 (may be
  * NULL; requires a context created with parents); both device or both host.  Device
  * buffers: asynchronous on `stream` (status via bfs_batch_wait or stats); host
- * buffers or stats: synchronizes.  BFS_ERR_OVERFLOW when a depth would exceed 254. */
+ * buffers (page-locked ones are written by the kernel directly) or stats:
+ * synchronizes.  BFS_ERR_OVERFLOW when a depth would exceed 254. */
 int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, uint8_t* depth, int32_t* parent,
                   bfs_batch_stats* stats, struct CUstream_st* stream);
 

@@ -128,9 +128,21 @@ int run_status(bfs_graph* g, RunHeader* h) {
 
 }  // namespace
 
-// Algorithmic HBM bytes of one run, from the per-level counters (the byte model
-// of the design notes): forward level 20*|F| + 8*m_f + 12*found (+ 16*found +
-// 8*parent_edges with PULL parents); backward level words*4 + 8*scanned +
+// Device address of page-locked host memory (written by kernels directly over the
+// host link), or null for device or pageable memory.
+void* pinned_device_ptr(void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+
+// Algorithmic HBM bytes of one run, from the per-level counters: forward level
+// 20*|F| + 8*m_f + 12*found (+ 16*found + 8*parent_edges with PULL parents);
+// backward level words*4 + 8*scanned +
 // 8*edges + 12*found; every level end 4 bitmap passes; a conversion one bitmap
 // pass + 4 per queue entry; the run's set-up 3 bitmap clears (+ 4*n_ni for
 // atomicMin parents) and the result pass 12*n + 8*reached + words*4.
@@ -297,8 +309,13 @@ extern "C" int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* pa
   const bool dd = is_device_ptr(depth), dp = is_device_ptr(parent);
   if (dd != dp) return fail(BFS_ERR_INVALID, "depth and parent must both be device or both be host memory");
   int rc;
+  int32_t* pd = dd ? nullptr : static_cast<int32_t*>(pinned_device_ptr(depth));
+  int32_t* pp = dd ? nullptr : static_cast<int32_t*>(pinned_device_ptr(parent));
   if (dd) {
     rc = launch_run(g, source, depth, parent, s);
+    if (rc) return rc;
+  } else if (pd && pp) {  // page-locked host buffers: the result pass writes them directly
+    rc = launch_run(g, source, pd, pp, s);
     if (rc) return rc;
   } else {
     if (!g->out_scratch) {

@@ -144,6 +144,7 @@ namespace bfsgb {
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+void* pinned_device_ptr(void* p);
 // Level-loop set-up and launch (bfs_run.cu).
 int configure_run(bfs_graph* g);
 // grid: CTAs of the cooperative launch (0 = the graph's full grid); out_depth8:

@@ -827,7 +827,13 @@ extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, ui
   int rc = BFS_OK;
   uint8_t* od = depth;
   int32_t* op = parent;
-  if (!dd) {
+  uint8_t* pd = dd ? nullptr : static_cast<uint8_t*>(pinned_device_ptr(depth));
+  int32_t* pp = (dd || !parent) ? nullptr : static_cast<int32_t*>(pinned_device_ptr(parent));
+  const bool direct = !dd && pd && (!parent || pp);  // page-locked host buffers, written directly
+  if (direct) {
+    od = pd;
+    op = pp;
+  } else if (!dd) {
     if (!b->out_depth) rc = balloc((void**)&b->out_depth, (size_t)kMsLanes * g->n, b, "alloc batch output");
     if (!rc && b->with_parents && !b->out_parent)
       rc = balloc((void**)&b->out_parent, (size_t)kMsLanes * g->n * 4, b, "alloc batch output");
@@ -845,7 +851,7 @@ extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, ui
     rc = ms_launch(b, sources, k, dl, op ? pl : nullptr, s, nullptr, &epoch);
   }
   cudaError_t e = cudaSuccess;
-  if (!rc && !dd) {
+  if (!rc && !dd && !direct) {
     e = cudaMemcpyAsync(depth, od, (size_t)k * g->n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && parent) e = cudaMemcpyAsync(parent, op, (size_t)k * g->n * 4, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) rc = cuda_fail(e, "copy batch results");

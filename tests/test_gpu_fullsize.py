@@ -4,7 +4,7 @@ the same 64 seeded sources, device-generated edges, default options.  16 of the
 sources are compared element by element with the oracle (depth, parent, the
 component edge count and every per-level counter); all 64 must give identical
 results for every TH of the sweep and for forced schedules (Sec. IV-B: the
-direction never changes the output).  Scale 26 (the spec graph) is
+direction never changes the output).  Scale 26 (the largest benchmark graph) is
 compared on two sources when BFS_RUN_SLOW=1."""
 import os
 
