@@ -316,6 +316,21 @@ def dist_setup():
     return ws, rank, local
 
 
+def replica_value(run_s, wall_s, edges, device):
+    """Replicas (one graph and one source set per rank, no data exchange): the
+    whole job's GTEPS = all ranks' traversed edges / the slowest rank's device
+    time.  Returns (value, max device seconds, max wall seconds)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([run_s, wall_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(edges)], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    run_max, wall_max = float(t[0]), float(t[1])
+    return float(e[0]) / run_max / 1e9, run_max, wall_max
+
+
 def run_reference(args, w, ws, rank):
     """CPU oracle arm: each step is one BFS of the oracle from one of the same
     seeded sources (a bounded sample of the workload)."""
@@ -641,14 +656,10 @@ def main():
     wall = t_all0.elapsed_time(t_all1) / 1e3
     run_s = sum(times)
     if ws > 1:
-        t = torch.tensor([run_s, wall], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        run_max, wall = float(t[0]), float(t[1])
-        edges = torch.tensor([float(sum(dw.ce) * args.steps)], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(edges)
-        value = float(edges[0]) / run_max / 1e9
+        value, run_max, wall = replica_value(run_s, wall, float(sum(dw.ce) * args.steps), "cuda")
     else:
         value = hmean(dw.gteps(times))
+        run_max = run_s
     k = len(dw.sources)
     model_total = sum(dw.model[i % k] for i in range(len(times)))
     achieved = model_total / run_s / 1e9
@@ -660,7 +671,7 @@ def main():
     paper_style = gmean([(16 << w["scale"]) / t / 1e9 for i, t in enumerate(times) if dw.levels[i % k] > 2])
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * run_s / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * run_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded RMAT, Graph500 parameters)",
         "config": dict(config_of(args.workload, w, dw.info),

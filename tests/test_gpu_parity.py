@@ -184,3 +184,36 @@ def test_repeated_runs_and_streams(rmat16):
         want_d, want_p = og.bfs(s)
         assert_same(d.cpu().numpy(), want_d, "depth")
         assert_same(p.cpu().numpy(), want_p, "parent")
+
+
+def test_pinned_host_buffers_match_oracle():
+    """Page-locked host result buffers are written by the kernel directly (no device
+    copy); the results are the oracle's, for the single-source and batched calls."""
+    torch = need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    scale = 14
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=214)
+    og = oracle.Graph(n, src, dst)
+    g = gpu_graph(n, src, dst, th=32)
+    mask = (np.diff(og.csr()[0]) > 0).astype(np.uint8)
+    sources = graphgen.sample_sources(mask, 6, seed=2141)
+    hd = torch.empty(n, dtype=torch.int32).pin_memory()
+    hp = torch.empty(n, dtype=torch.int32).pin_memory()
+    for s in sources:
+        want_d, want_p = og.bfs(int(s))
+        hd.fill_(7)
+        hp.fill_(7)
+        bfs.bfs_run(g.handle, int(s), hd, hp)
+        assert_same(hd.numpy(), want_d, "pinned depth (source %d)" % s)
+        assert_same(hp.numpy(), want_p, "pinned parent (source %d)" % s)
+    b = bfs.Batch(g)
+    bd = torch.empty((len(sources), n), dtype=torch.uint8).pin_memory()
+    bp = torch.empty((len(sources), n), dtype=torch.int32).pin_memory()
+    bfs.bfs_run_batch(b._h, sources, bd, bp)
+    want_d, want_p = og.bfs_batch_u8(sources)
+    for j in range(len(sources)):
+        assert_same(bd[j].numpy(), want_d[j], "pinned batch depth %d" % j)
+        assert_same(bp[j].numpy(), want_p[j], "pinned batch parent %d" % j)
+    b.close()
