@@ -36,7 +36,7 @@ struct __align__(64) MsSlot {
   unsigned long long nch;    // delegate chunk entries of the frontier
   unsigned long long mdone;  // degree of vertices every active lane has now reached
   unsigned long long ndl;    // deferred row chunks of the backward level
-  unsigned long long aux;    // slot 0: lanes with a non-isolated source
+  unsigned long long aux;    // lanes present in this level's frontier (slot 0: lanes with a non-isolated source)
 };
 
 // A chunk of a long row whose first kMsHead entries left some lane without a
@@ -234,43 +234,54 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
     const int64_t incl = warp_incl_scan(rest);
     const int64_t total = __shfl_sync(kFull, incl, 31);
     const int64_t excl = incl - rest;
-    for (int64_t base = 0; base < total; base += 32) {
+    // four 32-entry rounds per step: their column loads and frontier words are
+    // all in flight before the first round's scan
+    constexpr int kRounds = 4;
+    for (int64_t base = 0; base < total; base += 32 * kRounds) {
       if (!__any_sync(kFull, need != 0 && excl + rest > base)) break;
-      const int64_t e = base + lane;
-      int pos = 0;
+      int pos[kRounds], u[kRounds];
+      unsigned long long h[kRounds];
 #pragma unroll
-      for (int sh = 16; sh >= 1; sh >>= 1) {
-        const int64_t t = __shfl_sync(kFull, incl, pos + sh - 1);
-        if (t <= e) pos += sh;
-      }
-      const int64_t orb = __shfl_sync(kFull, rb, pos);
-      const int64_t oex = __shfl_sync(kFull, excl, pos);
-      const unsigned long long oneed = __shfl_sync(kFull, need, pos);
-      int u = -1;
-      unsigned long long h = 0;
-      if (e < total && oneed) {
-        u = __ldcs(p.col + orb + (e - oex));
-        h = Fc[u] & oneed;
-      }
-      unsigned long long sc = h;
+      for (int r = 0; r < kRounds; ++r) {
+        const int64_t e = base + 32 * r + lane;
+        int ps = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(kFull, sc, o);
-        const int ps = __shfl_up_sync(kFull, pos, o);
-        if (lane >= o && ps == pos) sc |= t;
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+          const int64_t t = __shfl_sync(kFull, incl, ps + sh - 1);
+          if (t <= e) ps += sh;
+        }
+        pos[r] = ps;
+        const int64_t orb = __shfl_sync(kFull, rb, ps);
+        const int64_t oex = __shfl_sync(kFull, excl, ps);
+        const unsigned long long oneed = __shfl_sync(kFull, need, ps);
+        u[r] = (e < total && oneed) ? __ldcs(p.col + orb + (e - oex)) : -1;
       }
-      unsigned long long before = __shfl_up_sync(kFull, sc, 1);
-      const int pprev = __shfl_up_sync(kFull, pos, 1);
-      if (lane == 0 || pprev != pos) before = 0;
-      const unsigned long long nb = h & ~before;
-      if (nb) ms_found(p, (int)(v0 + pos), nb, u, L);
-      // this step's part of the owner's row: lanes [lo, hi) - base; its last lane
-      // holds the OR of the part
-      const int64_t lo = max(excl, base), hi = min(excl + rest, base + 32);
-      const unsigned long long tot = __shfl_sync(kFull, sc, hi > lo ? (int)(hi - 1 - base) : lane);
-      if (hi > lo) {
-        found |= tot;
-        need &= ~tot;
+#pragma unroll
+      for (int r = 0; r < kRounds; ++r) h[r] = u[r] >= 0 ? Fc[u[r]] : 0ull;
+#pragma unroll
+      for (int r = 0; r < kRounds; ++r) {
+        const int64_t rbase = base + 32 * r;
+        const unsigned long long hh = h[r] & __shfl_sync(kFull, need, pos[r]);  // the owner's current need
+        unsigned long long sc = hh;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned long long t = __shfl_up_sync(kFull, sc, o);
+          const int ps = __shfl_up_sync(kFull, pos[r], o);
+          if (lane >= o && ps == pos[r]) sc |= t;
+        }
+        unsigned long long before = __shfl_up_sync(kFull, sc, 1);
+        const int pprev = __shfl_up_sync(kFull, pos[r], 1);
+        if (lane == 0 || pprev != pos[r]) before = 0;
+        const unsigned long long nb = hh & ~before;
+        if (nb) ms_found(p, (int)(v0 + pos[r]), nb, u[r], L);
+        // this round's part of the owner's row: lanes [lo, hi) - rbase; its last
+        // lane holds the OR of the part
+        const int64_t lo = max(excl, rbase), hi = min(excl + rest, rbase + 32);
+        const unsigned long long tot = __shfl_sync(kFull, sc, hi > lo ? (int)(hi - 1 - rbase) : lane);
+        if (hi > lo) {
+          found |= tot;
+          need &= ~tot;
+        }
       }
     }
     if (found) Fn[v] = found;
@@ -408,7 +419,7 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
   const int tid = threadIdx.x;
   if (tid < 6) s_red[tid] = 0;
   __syncthreads();
-  unsigned long long nfv = 0, mfv = 0, pairs = 0, pdeg = 0, mdone = 0;
+  unsigned long long nfv = 0, mfv = 0, pairs = 0, pdeg = 0, mdone = 0, act = 0;
   bool overflow = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < p.n_ni; b0 += stride) {  // CTA-uniform
@@ -419,6 +430,7 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
       Fo[v] = 0ull;
       fn = __ldcg(Fn + v);
       if (fn) {
+        act |= fn;
         const unsigned long long old = p.visit[v];
         p.visit[v] = old | fn;
         dg = p.deg[v];
@@ -451,6 +463,16 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
     }
   }
   if (overflow) set_failed(p, BFS_ERR_OVERFLOW);
+  {  // lanes present in the next frontier
+    __shared__ unsigned long long s_act;
+    if (tid == 0) s_act = 0ull;
+    __syncthreads();
+    const unsigned lo = __reduce_or_sync(kFull, (unsigned)act), hi = __reduce_or_sync(kFull, (unsigned)(act >> 32));
+    const unsigned long long w = ((unsigned long long)hi << 32) | lo;
+    if (lane_id() == 0 && w) atomicOr(&s_act, w);
+    __syncthreads();
+    if (tid == 0 && s_act) atomicOr(&sn->aux, s_act);
+  }
   const unsigned long long x[5] = {warp_sum(nfv), warp_sum(mfv), warp_sum(pairs), warp_sum(pdeg), warp_sum(mdone)};
   if (lane_id() == 0)
     for (int i = 0; i < 5; ++i)
@@ -531,7 +553,8 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     if (threadIdx.x == 0 && (L > 300 || gtimer() - t_start > p.run_timeout_ns)) set_failed(p, BFS_ERR_TIMEOUT);
     const bool bu = (bits & kMsBackward) != 0;
     if (bu) {
-      const int fl = ms_expand_bu(p, L, lanes);
+      // lanes whose frontier is empty can find no parent: they are not searched for
+      const int fl = ms_expand_bu(p, L, __ldcg(&p.slot[L & 3].aux));
       const int b2 = grid_sync(p, seq, [](int f) { return (f & 1) ? kMsDrain : 0; }, fl);
       if (b2 < 0) return;
       if (b2 & kMsDrain) {

@@ -150,6 +150,27 @@ def test_batch_deferred_long_rows(th):
     b.close()
 
 
+def test_batch_lanes_that_finish_early():
+    """Lanes whose source lies in a small component run out of frontier after a
+    few levels and are no longer searched for in backward levels; the other
+    lanes' results are unchanged (backward from level 1 on)."""
+    need_cuda()
+    scale = 12
+    n_big = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=312)
+    extra = [(n_big + i, n_big + i + 1) for i in range(3)] + [(n_big + 10, n_big + 11)]
+    e = np.asarray(extra, np.int32)
+    src = np.concatenate([src, e[:, 0]]).astype(np.int32)
+    dst = np.concatenate([dst, e[:, 1]]).astype(np.int32)
+    n = n_big + 20
+    og = oracle.Graph(n, src, dst)
+    g = gpu_graph(n, src, dst, th=16, alpha=1 << 30)
+    mask = (np.diff(og.csr()[0][: n_big + 1]) > 0).astype(np.uint8)
+    big = graphgen.sample_sources(mask, 60, seed=3121)
+    sources = list(big[:30]) + [n_big, n_big + 3, n_big + 10, n_big + 15] + list(big[30:])
+    _batch_check(og, g, sources)
+
+
 def test_batch_isolated_and_overflow():
     torch = need_cuda()
     import paper_1803_03922_gb300 as bfs
