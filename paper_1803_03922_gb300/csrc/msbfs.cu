@@ -172,14 +172,14 @@ __device__ void ms_expand_td(const MsParams& p, int L) {
 // h_i = F[u_i] & need gives each lane's first hit (bits set in h_i and not
 // before).  Column reads are streaming loads so they do not evict the frontier
 // words from L2.
-// A (lane, v) pair found by a backward level stores its parent's internal id u
-// as -(u + 1); forward levels store caller ids (>= 0, for atomicMin), and a pair
-// is found in exactly one level, so the result pass can tell them apart.
+// Parents are stored as caller ids, as forward levels need for atomicMin; one
+// caller_of gather serves every lane an entry settles.
 __device__ __forceinline__ void ms_found(const MsParams& p, int v, unsigned long long nb, int u, int L) {
+  const int pc = p.parent_i ? p.caller_of[u] : 0;
   while (nb) {
     const int b = __ffsll((long long)nb) - 1;
     nb &= nb - 1;
-    if (p.parent_i) p.parent_i[(int64_t)v * p.ls + b] = -(u + 1);
+    if (p.parent_i) p.parent_i[(int64_t)v * p.ls + b] = pc;
     p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
   }
 }
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
         const bool r = (vis >> j) & 1ull;
         uint8_t dv = r ? (uint8_t)((dq >> (8 * t)) & 0xFFu) : (uint8_t)255;
         int pv = -1;
-        if (r) pv = pv4[t] < 0 ? p.caller_of[-(pv4[t] + 1)] : pv4[t];
+        if (r) pv = pv4[t];
         if (c == p.src_c[j]) {
           dv = 0;
           pv = p.src_c[j];
