@@ -85,22 +85,40 @@ struct MsParams {
   int32_t* out_p[kMsLanes];  // lane j's parent row (when out_parents)
 };
 
-__device__ __forceinline__ unsigned long long* Fbuf(const MsParams& p, int i) {
-  return i == 0 ? p.F0 : (i == 1 ? p.F1 : p.F2);
+// Lane words: one bit per query, 64 lanes in an unsigned long long, or 32 in an
+// unsigned int for batches of at most 32 queries (half the per-vertex state
+// traffic of every sweep).  The state arrays hold 64-bit slots either way.
+template <typename W>
+__device__ __forceinline__ W* Fbuf(const MsParams& p, int i) {
+  return reinterpret_cast<W*>(i == 0 ? p.F0 : (i == 1 ? p.F1 : p.F2));
 }
+template <typename W>
+__device__ __forceinline__ W* visit_of(const MsParams& p) {
+  return reinterpret_cast<W*>(p.visit);
+}
+__device__ __forceinline__ int ffs_w(unsigned long long x) { return __ffsll((long long)x); }
+__device__ __forceinline__ int ffs_w(unsigned x) { return __ffs((int)x); }
+__device__ __forceinline__ int popc_w(unsigned long long x) { return __popcll(x); }
+__device__ __forceinline__ int popc_w(unsigned x) { return __popc(x); }
+__device__ __forceinline__ unsigned long long warp_or(unsigned long long x) {
+  const unsigned lo = __reduce_or_sync(kFull, (unsigned)x), hi = __reduce_or_sync(kFull, (unsigned)(x >> 32));
+  return ((unsigned long long)hi << 32) | lo;
+}
+__device__ __forceinline__ unsigned long long warp_or(unsigned x) { return __reduce_or_sync(kFull, x); }
 
 // Offers caller id pc as parent of v to every lane of nb (forward levels).
-__device__ __forceinline__ void ms_offer(const MsParams& p, int v, unsigned long long nb, int pc) {
+template <typename W>
+__device__ __forceinline__ void ms_offer(const MsParams& p, int v, W nb, int pc) {
   while (nb) {
-    const int b = __ffsll((long long)nb) - 1;
+    const int b = ffs_w(nb) - 1;
     nb &= nb - 1;
     atomicMin(p.parent_i + (int64_t)v * p.ls + b, pc);
   }
 }
 
-__device__ __forceinline__ void ms_push(const MsParams& p, unsigned long long fu, int pc, int v,
-                                        unsigned long long* __restrict__ Fn) {
-  const unsigned long long nb = fu & ~p.visit[v];
+template <typename W>
+__device__ __forceinline__ void ms_push(const MsParams& p, W fu, int pc, int v, W* __restrict__ Fn) {
+  const W nb = fu & ~visit_of<W>(p)[v];
   if (!nb) return;
   atomicOr(Fn + v, nb);
   if (p.parent_i) ms_offer(p, v, nb, pc);
@@ -109,10 +127,11 @@ __device__ __forceinline__ void ms_push(const MsParams& p, unsigned long long fu
 // Forward level: delegate chunks, then the normal frontier vertices gathered 32
 // per warp (lane i owns vertex w0+i when its frontier word is nonzero; the warp
 // walks the owned rows' entries 32 at a time).
+template <typename W>
 __device__ void ms_expand_td(const MsParams& p, int L) {
   const MsSlot* sc = p.slot + (L & 3);
-  const unsigned long long* Fc = Fbuf(p, L % 3);
-  unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
+  const W* Fc = Fbuf<W>(p, L % 3);
+  W* Fn = Fbuf<W>(p, (L + 1) % 3);
   const int2* CL = (L & 1) ? p.CL1 : p.CL0;
   const int lane = lane_id();
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -123,7 +142,7 @@ __device__ void ms_expand_td(const MsParams& p, int L) {
     if (it < nch) {
       const int2 ck = CL[it];
       const int u = ck.x;
-      const unsigned long long fu = Fc[u];
+      const W fu = Fc[u];
       const int pc = p.parent_i ? p.caller_of[u] : 0;
       const int64_t rb = p.off[u], re = rb + p.deg[u];
       const int64_t beg = rb + (int64_t)ck.y * kChunk, end = min(beg + kChunk, re);
@@ -132,7 +151,7 @@ __device__ void ms_expand_td(const MsParams& p, int L) {
     }
     const int64_t u0 = p.d + (it - nch) * 32;
     const int64_t u = u0 + lane;
-    unsigned long long fu = 0;
+    W fu = 0;
     int64_t beg = 0, deg = 0;
     int pc = 0;
     if (u < p.n_ni) {
@@ -156,7 +175,7 @@ __device__ void ms_expand_td(const MsParams& p, int L) {
       }
       const int64_t ob = __shfl_sync(kFull, beg, pos);
       const int64_t ox = __shfl_sync(kFull, excl, pos);
-      const unsigned long long ofu = __shfl_sync(kFull, fu, pos);
+      const W ofu = __shfl_sync(kFull, fu, pos);
       const int opc = __shfl_sync(kFull, pc, pos);
       if (e < total) ms_push(p, ofu, opc, __ldcs(p.col + ob + (e - ox)), Fn);
     }
@@ -174,10 +193,11 @@ __device__ void ms_expand_td(const MsParams& p, int L) {
 // words from L2.
 // Parents are stored as caller ids, as forward levels need for atomicMin; one
 // caller_of gather serves every lane an entry settles.
-__device__ __forceinline__ void ms_found(const MsParams& p, int v, unsigned long long nb, int u, int L) {
+template <typename W>
+__device__ __forceinline__ void ms_found(const MsParams& p, int v, W nb, int u, int L) {
   const int pc = p.parent_i ? p.caller_of[u] : 0;
   while (nb) {
-    const int b = __ffsll((long long)nb) - 1;
+    const int b = ffs_w(nb) - 1;
     nb &= nb - 1;
     if (p.parent_i) p.parent_i[(int64_t)v * p.ls + b] = pc;
     p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
@@ -185,11 +205,12 @@ __device__ __forceinline__ void ms_found(const MsParams& p, int v, unsigned long
 }
 
 // Returns 1 in a thread that deferred row chunks.
-__device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) {
+template <typename W>
+__device__ int ms_expand_bu(const MsParams& p, int L, W lanes) {
   MsSlot* sc = p.slot + (L & 3);
   int deferred = 0;
-  const unsigned long long* Fc = Fbuf(p, L % 3);
-  unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
+  const W* Fc = Fbuf<W>(p, L % 3);
+  W* Fn = Fbuf<W>(p, (L + 1) % 3);
   const int lane = lane_id();
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -203,10 +224,10 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
   for (int64_t it = gwarp; it < nbatch; it += nwarps) {  // warp-uniform
     const int64_t v0 = p.d + it * 32;
     const int64_t v = v0 + lane;
-    unsigned long long need = 0, found = 0;
+    W need = 0, found = 0;
     int64_t beg = 0, end = 0;
     if (v < p.n_ni) {
-      need = lanes & ~p.visit[v];
+      need = lanes & ~visit_of<W>(p)[v];
       if (need) {
         beg = p.off[v];
         end = beg + p.deg[v];
@@ -214,14 +235,14 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
     }
     if (need) {
       int u[4];
-      unsigned long long h[4];
+      W h[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) u[t] = beg + t < end ? __ldcs(p.col + beg + t) : -1;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? Fc[u[t]] : 0ull;
+      for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? Fc[u[t]] : (W)0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const unsigned long long x = h[t] & need;
+        const W x = h[t] & need;
         if (x) {
           ms_found(p, (int)v, x, u[t], L);
           found |= x;
@@ -240,7 +261,7 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
     for (int64_t base = 0; base < total; base += 32 * kRounds) {
       if (!__any_sync(kFull, need != 0 && excl + rest > base)) break;
       int pos[kRounds], u[kRounds];
-      unsigned long long h[kRounds];
+      W h[kRounds];
 #pragma unroll
       for (int r = 0; r < kRounds; ++r) {
         const int64_t e = base + 32 * r + lane;
@@ -253,31 +274,31 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
         pos[r] = ps;
         const int64_t orb = __shfl_sync(kFull, rb, ps);
         const int64_t oex = __shfl_sync(kFull, excl, ps);
-        const unsigned long long oneed = __shfl_sync(kFull, need, ps);
+        const W oneed = __shfl_sync(kFull, need, ps);
         u[r] = (e < total && oneed) ? __ldcs(p.col + orb + (e - oex)) : -1;
       }
 #pragma unroll
-      for (int r = 0; r < kRounds; ++r) h[r] = u[r] >= 0 ? Fc[u[r]] : 0ull;
+      for (int r = 0; r < kRounds; ++r) h[r] = u[r] >= 0 ? Fc[u[r]] : (W)0;
 #pragma unroll
       for (int r = 0; r < kRounds; ++r) {
         const int64_t rbase = base + 32 * r;
-        const unsigned long long hh = h[r] & __shfl_sync(kFull, need, pos[r]);  // the owner's current need
-        unsigned long long sc = hh;
+        const W hh = h[r] & __shfl_sync(kFull, need, pos[r]);  // the owner's current need
+        W sc = hh;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long t = __shfl_up_sync(kFull, sc, o);
+          const W t = __shfl_up_sync(kFull, sc, o);
           const int ps = __shfl_up_sync(kFull, pos[r], o);
           if (lane >= o && ps == pos[r]) sc |= t;
         }
-        unsigned long long before = __shfl_up_sync(kFull, sc, 1);
+        W before = __shfl_up_sync(kFull, sc, 1);
         const int pprev = __shfl_up_sync(kFull, pos[r], 1);
         if (lane == 0 || pprev != pos[r]) before = 0;
-        const unsigned long long nb = hh & ~before;
+        const W nb = hh & ~before;
         if (nb) ms_found(p, (int)(v0 + pos[r]), nb, u[r], L);
         // this round's part of the owner's row: lanes [lo, hi) - rbase; its last
         // lane holds the OR of the part
         const int64_t lo = max(excl, rbase), hi = min(excl + rest, rbase + 32);
-        const unsigned long long tot = __shfl_sync(kFull, sc, hi > lo ? (int)(hi - 1 - rbase) : lane);
+        const W tot = __shfl_sync(kFull, sc, hi > lo ? (int)(hi - 1 - rbase) : lane);
         if (hi > lo) {
           found |= tot;
           need &= ~tot;
@@ -291,15 +312,15 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
   const int64_t items = ((int64_t)p.d + 31) / 32;
   for (int64_t it = gwarp; it < items; it += nwarps) {
     const int64_t v = it * 32 + lane;
-    const unsigned long long need_l = v < p.d ? (lanes & ~p.visit[v]) : 0ull;
+    const W need_l = v < p.d ? (lanes & ~visit_of<W>(p)[v]) : (W)0;
     unsigned pend = __ballot_sync(kFull, need_l != 0);
     while (pend) {
       const int j = __ffs(pend) - 1;
       pend &= pend - 1;
       const int vv = (int)(it * 32 + j);
-      unsigned long long need = __shfl_sync(kFull, need_l, j);
+      W need = __shfl_sync(kFull, need_l, j);
       const int64_t beg = p.off[vv], end = beg + p.deg[vv];
-      unsigned long long found = 0;
+      W found = 0;
       const int64_t al = beg & ~(int64_t)3, hend = min(end, al + kMsHead);
       // 128 entries per step: lane l holds entries 4l..4l+3 of the step (one
       // 128-bit load), in row order within the lane, lanes in order along the row
@@ -309,40 +330,40 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
         if (jj < hend) c4 = __ldcs(reinterpret_cast<const int4*>(p.col + jj));
         const int u[4] = {jj >= beg ? c4.x : -1, (jj + 1 >= beg && jj + 1 < hend) ? c4.y : -1,
                           (jj + 2 >= beg && jj + 2 < hend) ? c4.z : -1, (jj + 3 >= beg && jj + 3 < hend) ? c4.w : -1};
-        unsigned long long h[4];
+        W h[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? (Fc[u[t]] & need) : 0ull;
-        const unsigned long long mine = h[0] | h[1] | h[2] | h[3];
-        unsigned long long incl = mine;
+        for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? (Fc[u[t]] & need) : (W)0;
+        const W mine = h[0] | h[1] | h[2] | h[3];
+        W incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-          const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+          const W t = __shfl_up_sync(kFull, incl, o);
           if (lane >= o) incl |= t;
         }
-        unsigned long long before = __shfl_up_sync(kFull, incl, 1);
+        W before = __shfl_up_sync(kFull, incl, 1);
         if (lane == 0) before = 0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          const unsigned long long nb = h[t] & ~before;
+          const W nb = h[t] & ~before;
           if (nb) ms_found(p, vv, nb, u[t], L);
           before |= h[t];
         }
-        const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+        const W tot = __shfl_sync(kFull, incl, 31);
         found |= tot;
         need &= ~tot;
       }
       if (lane == 0 && found) Fn[vv] = found;
       if (need && hend < end) {
         const int nc = (int)((end - hend + kChunk - 1) / kChunk);
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&sc->ndl, (unsigned long long)nc);
-        base = __shfl_sync(kFull, base, 0);
+        W dbase = 0;
+        if (lane == 0) dbase = atomicAdd(&sc->ndl, (W)nc);
+        dbase = __shfl_sync(kFull, dbase, 0);
         for (int c = lane; c < nc; c += 32) {
           MsDefer e;
           e.v = vv;
           e.c = c;
           e.need = need;
-          p.DL[base + c] = e;
+          p.DL[dbase + c] = e;
         }
         deferred = 1;
       }
@@ -355,10 +376,11 @@ __device__ int ms_expand_bu(const MsParams& p, int L, unsigned long long lanes) 
 // found bits are in F_next).  Chunks of one row run on different warps, so a
 // lane's canonical parent (first hit in row order = smallest caller id) is the
 // atomicMin of the chunks' first hits, in caller ids as in forward levels.
+template <typename W>
 __device__ void ms_drain_bu(const MsParams& p, int L) {
   const MsSlot* sc = p.slot + (L & 3);
-  const unsigned long long* Fc = Fbuf(p, L % 3);
-  unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
+  const W* Fc = Fbuf<W>(p, L % 3);
+  W* Fn = Fbuf<W>(p, (L + 1) % 3);
   const int lane = lane_id();
   const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -366,7 +388,7 @@ __device__ void ms_drain_bu(const MsParams& p, int L) {
   for (int64_t it = gwarp; it < nd; it += nwarps) {
     const MsDefer e = p.DL[it];
     const int v = e.v;
-    unsigned long long need = e.need, found = 0;
+    W need = (W)e.need, found = 0;
     const int64_t beg = p.off[v], end = beg + p.deg[v];
     const int64_t c0 = (beg & ~(int64_t)3) + kMsHead + (int64_t)e.c * kChunk;
     const int64_t c1 = min(c0 + kChunk, end);
@@ -375,31 +397,31 @@ __device__ void ms_drain_bu(const MsParams& p, int L) {
       int4 c4 = make_int4(-1, -1, -1, -1);
       if (jj < c1) c4 = __ldcs(reinterpret_cast<const int4*>(p.col + jj));
       const int u[4] = {c4.x, jj + 1 < c1 ? c4.y : -1, jj + 2 < c1 ? c4.z : -1, jj + 3 < c1 ? c4.w : -1};
-      unsigned long long h[4];
+      W h[4];
 #pragma unroll
       for (int t = 0; t < 4; ++t) h[t] = u[t] >= 0 ? (Fc[u[t]] & need) : 0ull;
-      unsigned long long incl = h[0] | h[1] | h[2] | h[3];
+      W incl = h[0] | h[1] | h[2] | h[3];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(kFull, incl, o);
+        const W t = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl |= t;
       }
-      unsigned long long before = __shfl_up_sync(kFull, incl, 1);
+      W before = __shfl_up_sync(kFull, incl, 1);
       if (lane == 0) before = 0;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        unsigned long long nb = h[t] & ~before;
+        W nb = h[t] & ~before;
         before |= h[t];
         if (!nb) continue;
         const int pc = p.parent_i ? p.caller_of[u[t]] : 0;
         while (nb) {
-          const int b = __ffsll((long long)nb) - 1;
+          const int b = ffs_w(nb) - 1;
           nb &= nb - 1;
           if (p.parent_i) atomicMin(p.parent_i + (int64_t)v * p.ls + b, pc);
           p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
         }
       }
-      const unsigned long long tot = __shfl_sync(kFull, incl, 31);
+      const W tot = __shfl_sync(kFull, incl, 31);
       found |= tot;
       need &= ~tot;
     }
@@ -409,41 +431,45 @@ __device__ void ms_drain_bu(const MsParams& p, int L) {
 
 // Level end: merge F_next into visit, clear the frontier word two levels back,
 // (forward) write depths, count the next frontier and list its delegate chunks.
-__device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long long lanes) {
+template <typename W>
+__device__ void ms_level_end(const MsParams& p, int L, bool td, W lanes) {
   __shared__ unsigned long long s_red[6];
   __shared__ unsigned long long s_base;
-  unsigned long long* Fn = Fbuf(p, (L + 1) % 3);
-  unsigned long long* Fo = Fbuf(p, (L + 2) % 3);
+  W* Fn = Fbuf<W>(p, (L + 1) % 3);
+  W* Fo = Fbuf<W>(p, (L + 2) % 3);
+  W* visit = visit_of<W>(p);
   int2* CLn = (L & 1) ? p.CL0 : p.CL1;
   MsSlot* sn = p.slot + ((L + 1) & 3);
   const int tid = threadIdx.x;
   if (tid < 6) s_red[tid] = 0;
   __syncthreads();
-  unsigned long long nfv = 0, mfv = 0, pairs = 0, pdeg = 0, mdone = 0, act = 0;
+  unsigned long long nfv = 0, mfv = 0, pairs = 0, pdeg = 0, mdone = 0;
+  W act = 0;
   bool overflow = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < p.n_ni; b0 += stride) {  // CTA-uniform
     const int64_t v = b0 + tid;
-    unsigned long long fn = 0, nch = 0;
+    W fn = 0;
+    unsigned long long nch = 0;
     int dg = 0;
     if (v < p.n_ni) {
-      Fo[v] = 0ull;
+      Fo[v] = 0;
       fn = __ldcg(Fn + v);
       if (fn) {
         act |= fn;
-        const unsigned long long old = p.visit[v];
-        p.visit[v] = old | fn;
+        const W old = visit[v];
+        visit[v] = old | fn;
         dg = p.deg[v];
         nfv += 1;
         mfv += (unsigned long long)dg;
-        pairs += (unsigned long long)__popcll(fn);
-        pdeg += (unsigned long long)__popcll(fn) * (unsigned long long)dg;
+        pairs += (unsigned long long)popc_w(fn);
+        pdeg += (unsigned long long)popc_w(fn) * (unsigned long long)dg;
         if ((old | fn) == lanes && old != lanes) mdone += (unsigned long long)dg;
         if (L + 1 > 254) overflow = true;
         if (td) {
-          unsigned long long x = fn;
+          W x = fn;
           while (x) {
-            const int b = __ffsll((long long)x) - 1;
+            const int b = ffs_w(x) - 1;
             x &= x - 1;
             p.depth_i[(int64_t)v * p.ls + b] = (uint8_t)(L + 1);
           }
@@ -467,8 +493,7 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
     __shared__ unsigned long long s_act;
     if (tid == 0) s_act = 0ull;
     __syncthreads();
-    const unsigned lo = __reduce_or_sync(kFull, (unsigned)act), hi = __reduce_or_sync(kFull, (unsigned)(act >> 32));
-    const unsigned long long w = ((unsigned long long)hi << 32) | lo;
+    const unsigned long long w = warp_or(act);
     if (lane_id() == 0 && w) atomicOr(&s_act, w);
     __syncthreads();
     if (tid == 0 && s_act) atomicOr(&sn->aux, s_act);
@@ -489,7 +514,10 @@ __device__ void ms_level_end(const MsParams& p, int L, bool td, unsigned long lo
 
 constexpr int kMsBackward = 1, kMsDone = 2, kMsDrain = 4;
 
+template <typename W>
 __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
+  W* visit = visit_of<W>(p);
+  W* F0 = Fbuf<W>(p, 0);
   __shared__ long long s_mu;
   __shared__ unsigned long long s_pairs, s_pdeg;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -497,11 +525,15 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned seq = 0;
   // set-up: state words, parent slots
-  for (int64_t v = gtid; v < p.n_ni; v += gthreads) {
-    p.visit[v] = 0ull;
-    p.F0[v] = 0ull;
-    p.F1[v] = 0ull;
-    p.F2[v] = 0ull;
+  {
+    W* F1 = Fbuf<W>(p, 1);
+    W* F2 = Fbuf<W>(p, 2);
+    for (int64_t v = gtid; v < p.n_ni; v += gthreads) {
+      visit[v] = 0;
+      F0[v] = 0;
+      F1[v] = 0;
+      F2[v] = 0;
+    }
   }
   if (p.parent_i) {
     const int64_t P4 = (int64_t)p.n_ni * (p.ls / 4);
@@ -514,21 +546,22 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   }
   if (grid_sync(p, seq, no_master) < 0) return;
   if (leader) {  // seed the k sources (a source may repeat across lanes)
-    unsigned long long nfv = 0, mfv = 0, nch = 0, pdeg = 0, act = 0;
+    unsigned long long nfv = 0, mfv = 0, nch = 0, pdeg = 0;
+    W act = 0;
     for (int j = 0; j < p.k; ++j) {
       const int v = p.internal_of[p.src_c[j]];
       if (v >= p.n_ni) continue;  // an isolated source: its lane is finished
-      const unsigned long long bit = 1ull << j;
+      const W bit = (W)1 << j;
       act |= bit;
       const int dg = p.deg[v];
-      if (p.F0[v] == 0) {
+      if (F0[v] == 0) {
         nfv += 1;
         mfv += (unsigned long long)dg;
         if (v < p.d)
           for (int64_t c = 0; c < ((int64_t)dg + kChunk - 1) / kChunk; ++c) p.CL0[nch++] = make_int2(v, (int)c);
       }
-      p.F0[v] |= bit;
-      p.visit[v] |= bit;
+      F0[v] |= bit;
+      visit[v] |= bit;
       p.depth_i[(int64_t)v * p.ls + j] = 0;
       if (p.parent_i) p.parent_i[(int64_t)v * p.ls + j] = p.src_c[j];
       pdeg += (unsigned long long)dg;
@@ -544,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   int bits = grid_sync(p, seq, [&](int) { return p.slot[0].nfv ? 0 : kMsDone; });
   if (bits < 0) return;
   __shared__ unsigned long long s_tb, s_te;
-  const unsigned long long lanes = __ldcg(&p.slot[0].aux);  // lanes with a non-isolated source
+  const W lanes = (W)__ldcg(&p.slot[0].aux);  // lanes with a non-isolated source
   const unsigned long long t_start = gtimer();
   if (leader) p.hdr->t_init = t_start;
   int L = 0;
@@ -554,19 +587,19 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
     const bool bu = (bits & kMsBackward) != 0;
     if (bu) {
       // lanes whose frontier is empty can find no parent: they are not searched for
-      const int fl = ms_expand_bu(p, L, __ldcg(&p.slot[L & 3].aux));
+      const int fl = ms_expand_bu<W>(p, L, (W)__ldcg(&p.slot[L & 3].aux));
       const int b2 = grid_sync(p, seq, [](int f) { return (f & 1) ? kMsDrain : 0; }, fl);
       if (b2 < 0) return;
       if (b2 & kMsDrain) {
-        ms_drain_bu(p, L);
+        ms_drain_bu<W>(p, L);
         if (grid_sync(p, seq, no_master) < 0) return;
       }
     } else {
-      ms_expand_td(p, L);
+      ms_expand_td<W>(p, L);
       if (grid_sync(p, seq, no_master) < 0) return;
     }
     if (leader) s_te = gtimer();
-    ms_level_end(p, L, !bu, lanes);
+    ms_level_end<W>(p, L, !bu, lanes);
     if (leader) p.slot[(L + 2) & 3] = MsSlot();
     bits = grid_sync(p, seq, [&](int) {
       const MsSlot* sc = p.slot + (L & 3);
@@ -599,11 +632,11 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
   for (int64_t c = gtid; c < p.n; c += gthreads) {
     const int v = p.internal_of[c];
     const bool in = v < p.n_ni;
-    const unsigned long long vis = in ? p.visit[v] : 0ull;
+    const W vis = in ? visit[v] : (W)0;
     for (int j0 = 0; j0 < p.k; j0 += 4) {
       unsigned dq = 0xFFFFFFFFu;
       int4 pq = make_int4(-1, -1, -1, -1);
-      if (in && ((vis >> j0) & 0xFull)) {
+      if (in && ((vis >> j0) & 0xFu)) {
         dq = *reinterpret_cast<const unsigned*>(p.depth_i + (int64_t)v * p.ls + j0);
         if (p.out_parents) pq = *reinterpret_cast<const int4*>(p.parent_i + (int64_t)v * p.ls + j0);
       }
@@ -678,6 +711,15 @@ int balloc(void** p, size_t bytes, bfs_batch* b, const char* what) {
   return BFS_OK;
 }
 
+// Resident CTAs per SM of the batched kernel: the smaller of its two lane widths.
+cudaError_t ms_occupancy(int* per_sm) {
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, ms_bfs_loop<unsigned long long>, kThreads, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ms_bfs_loop<unsigned>, kThreads, 0);
+  *per_sm = a < b ? a : b;
+  return e;
+}
+
 bool dev_ptr(const void* q) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
@@ -694,7 +736,7 @@ extern "C" int bfs_batch_capacity(int32_t* ctas) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_loop, kThreads, 0);
+  if (e == cudaSuccess) e = ms_occupancy(&per_sm);
   if (e != cudaSuccess) return cuda_fail(e, "bfs_batch_capacity");
   *ctas = sms * (per_sm < 2 ? per_sm : 2);
   return BFS_OK;
@@ -733,7 +775,7 @@ extern "C" int bfs_batch_create(const bfs_graph* g, int32_t with_parents, int32_
   if (!rc) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms_bfs_loop, kThreads, 0);
+    cudaError_t e = ms_occupancy(&per_sm);
     if (e != cudaSuccess) rc = cuda_fail(e, "occupancy");
     else if (per_sm < 1) rc = fail(BFS_ERR_CUDA, "multi-source kernel does not fit on an SM");
     else {
@@ -821,7 +863,8 @@ int ms_launch(bfs_batch* b, const int32_t* sources, int k, uint8_t* const* depth
   }
   void* args[] = {&p};
   if (e == cudaSuccess)
-    e = cudaLaunchCooperativeKernel((const void*)ms_bfs_loop, dim3(b->grid), dim3(kThreads), args, 0, s);
+    e = cudaLaunchCooperativeKernel(k <= 32 ? (const void*)ms_bfs_loop<unsigned> : (const void*)ms_bfs_loop<unsigned long long>,
+                                    dim3(b->grid), dim3(kThreads), args, 0, s);
   if (e == cudaSuccess && hdr_out) e = cudaMemcpyAsync(hdr_out, b->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail(e, "multi-source launch");
   if (epoch_out) *epoch_out = p.epoch;
