@@ -20,7 +20,7 @@ from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 RUN_SPACE: Dict[str, Sequence] = {
     "alpha": (5, 10, 15, 30, 60),
     "beta": (9, 18, 36, 72),
-    "blocks_per_sm": (2, 3),
+    "blocks_per_sm": (1, 2, 3),
 }
 PAPER_FACTOR0 = (0.05, 0.1, 0.5, 1.0, 2.0)
 TH_SPACE = (32, 64, 128, 256)

@@ -60,8 +60,8 @@ int check_options(const bfs_options& o) {
   if (o.alpha <= 0 || o.beta <= 0) return fail(BFS_ERR_INVALID, "alpha and beta must be > 0");
   if (o.td_parent != BFS_TD_PARENT_PULL && o.td_parent != BFS_TD_PARENT_ATOMICMIN)
     return fail(BFS_ERR_INVALID, "unknown td_parent");
-  if (o.blocks_per_sm < 0 || o.blocks_per_sm == 1 || o.blocks_per_sm > 3)
-    return fail(BFS_ERR_INVALID, "blocks_per_sm must be 0, 2 or 3");
+  if (o.blocks_per_sm < 0 || o.blocks_per_sm > 3)
+    return fail(BFS_ERR_INVALID, "blocks_per_sm must be 0, 1, 2 or 3");
   if (o.barrier_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "barrier_timeout_ms must be > 0");
   if (o.run_timeout_ms <= 0) return fail(BFS_ERR_INVALID, "run_timeout_ms must be > 0");
   if (!(o.factor0 >= 0) || !(o.factor1 >= 0)) return fail(BFS_ERR_INVALID, "factors must be >= 0");

@@ -12,6 +12,7 @@ namespace bfsgb {
 
 constexpr int kThreads = 512;         // level-loop CTA size (16 warps)
 constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kMaxWarpsPerBlock = 32;  // shared arrays indexed by warp fit 1024-thread CTAs
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
 constexpr int kHead = 4;              // row entries kept in the per-vertex head record

@@ -517,7 +517,7 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
 // scans spread over the grid instead of stalling the warp that met them.
 __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
                           uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc) {
-  __shared__ unsigned s_found[kWarpsPerBlock][32];
+  __shared__ unsigned s_found[kMaxWarpsPerBlock][32];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
   unsigned* found = s_found[threadIdx.x >> 5];
@@ -759,8 +759,8 @@ __device__ void run_body(const BfsParams& p);
 
 // Two builds of the same kernel: 2 CTAs of 512 threads per SM (64 registers) or
 // 3 (40 registers, some spilled to local memory).
-template <int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) bfs_level_loop(BfsParams p) {
+template <int kMinBlocks, int kThr>
+__global__ void __launch_bounds__(kThr, kMinBlocks) bfs_level_loop(BfsParams p) {
   run_body(p);
 }
 
@@ -1023,9 +1023,10 @@ int configure_run(bfs_graph* g) {
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   if (!coop) return fail(BFS_ERR_CUDA, "device does not support cooperative launch");
-  const int variant = g->opt.blocks_per_sm == 3 ? 3 : 2;
-  e = variant == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<3>, kThreads, 0)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<2>, kThreads, 0);
+  const int variant = g->opt.blocks_per_sm == 3 ? 3 : (g->opt.blocks_per_sm == 1 ? 1 : 2);
+  if (variant == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<3, kThreads>, kThreads, 0);
+  else if (variant == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<1, 2 * kThreads>, 2 * kThreads, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<2, kThreads>, kThreads, 0);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   if (per_sm < 1) return fail(BFS_ERR_CUDA, "level-loop kernel does not fit on an SM");
   const int want = per_sm < variant ? per_sm : variant;
@@ -1089,9 +1090,14 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
     if (e0 != cudaSuccess) return cuda_fail(e0, "reset barrier words");
   }
   void* args[] = {&p};
-  const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3> : (const void*)bfs_level_loop<2>;
-  const int blocks = grid > 0 && grid < g->grid_blocks ? grid : g->grid_blocks;
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kThreads), args, 0, s);
+  const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3, kThreads>
+                   : g->variant == 1 ? (const void*)bfs_level_loop<1, 2 * kThreads>
+                                     : (const void*)bfs_level_loop<2, kThreads>;
+  // grid is counted in 512-thread CTAs (the serving slices); a 1024-thread CTA takes two
+  const int want = g->variant == 1 ? (grid + 1) / 2 : grid;
+  const int blocks = want > 0 && want < g->grid_blocks ? want : g->grid_blocks;
+  const int threads = g->variant == 1 ? 2 * kThreads : kThreads;
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
   return BFS_OK;
 }

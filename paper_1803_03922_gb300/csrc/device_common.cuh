@@ -133,7 +133,7 @@ __device__ __forceinline__ int no_master(int) { return 0; }
 // CTA totals.  Called by all threads of the CTA.
 __device__ inline void block_scan2(unsigned long long a, unsigned long long b, unsigned long long& ea,
                             unsigned long long& eb, unsigned long long& ta, unsigned long long& tb) {
-  __shared__ unsigned long long s_a[kWarpsPerBlock], s_b[kWarpsPerBlock];
+  __shared__ unsigned long long s_a[kMaxWarpsPerBlock], s_b[kMaxWarpsPerBlock];
   const int lane = lane_id(), wid = threadIdx.x >> 5;
   unsigned long long ia = a, ib = b;
 #pragma unroll
@@ -151,7 +151,8 @@ __device__ inline void block_scan2(unsigned long long a, unsigned long long b, u
   __syncthreads();
   unsigned long long pa = 0, pb = 0;
   ta = tb = 0;
-  for (int w = 0; w < kWarpsPerBlock; ++w) {
+  const int nw = (int)(blockDim.x >> 5);
+  for (int w = 0; w < nw; ++w) {
     if (w < wid) {
       pa += s_a[w];
       pb += s_b[w];

@@ -217,3 +217,16 @@ def test_pinned_host_buffers_match_oracle():
         assert_same(bd[j].numpy(), want_d[j], "pinned batch depth %d" % j)
         assert_same(bp[j].numpy(), want_p[j], "pinned batch parent %d" % j)
     b.close()
+
+
+@pytest.mark.parametrize("bps", [1, 3])
+def test_other_level_loop_builds_match_oracle(rmat16, bps):
+    """The 1024-thread (one CTA per SM) and 40-register (three per SM) builds of
+    the level loop give the oracle's results, counters included."""
+    n, src, dst, og, sources = rmat16
+    g = gpu_graph(n, src, dst, th=64, blocks_per_sm=bps)
+    check_against_oracle(og, g, sources[:16], stats=True, th=64)
+    for sched in ("bottomup", "alternate"):
+        g.set_options(**SCHEDULES[sched])
+        check_against_oracle(og, g, sources[:4])
+    g.close()
