@@ -27,6 +27,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -304,7 +305,22 @@ def cpu_oracle_sample(w, host_edges, sources, ce_dev, budget_s=20.0, max_sources
     return {"value": hmean(vals), "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": "%d of the %d sources on the same graph (single-threaded C, -O2; host graph build "
                       "%.1f s untimed)" % (used, len(sources), build_s),
-            "seconds": spent}
+            "seconds": spent, "host": host_cpu()}
+
+
+def host_cpu():
+    """The host's CPU model and logical core count (the CPU baseline runs on one)."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip() or model
+                    break
+    except OSError:
+        pass
+    return {"model": model, "arch": platform.machine(), "nproc": os.cpu_count()}
 
 
 # ---- main arms ------------------------------------------------------------------------------
@@ -365,7 +381,7 @@ def run_reference(args, w, ws, rank):
         "config": config_of(args.workload, w),
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "GTEPS",
                          "sample": "one of the 64 seeded sources per step on the same graph "
-                                   "(single-threaded C, -O2)"},
+                                   "(single-threaded C, -O2)", "host": host_cpu()},
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -758,6 +774,17 @@ def main():
             extras["rmat22_th%d" % th] = {"gteps": hmean(d2.gteps(t2)), "delegates": d2.info.delegates,
                                           "roofline_frac": sum(d2.model) / sum(t2) / 1e9 / peak}
             d2.close()
+        try:  # config 1: RMAT scale 16, top-down only, 64 sources
+            w16 = dict(WORKLOADS["rmat16"])
+            d1 = DeviceWorkload("rmat16", w16, rank)
+            d1.g.set_options(schedule=1)
+            d1.timed(1, flush, stream)
+            t1 = d1.timed(2, flush, stream)
+            extras["rmat16_topdown"] = {"gteps": hmean(d1.gteps(t1)),
+                                        "ms_per_bfs_median": 1e3 * statistics.median(t1)}
+            d1.close()
+        except Exception as e:  # report, do not hide
+            extras["rmat16_topdown"] = {"error": str(e)}
         if args.workload == "rmat22":
             try:
                 extras["autotuned_rmat22"] = autotuned(w, rank, flush, stream, peak)

@@ -230,3 +230,41 @@ def test_other_level_loop_builds_match_oracle(rmat16, bps):
         g.set_options(**SCHEDULES[sched])
         check_against_oracle(og, g, sources[:4])
     g.close()
+
+
+def test_depth_invariant_under_relabeling():
+    """Metamorphic: relabelling the vertices by a permutation pi leaves every hop
+    distance unchanged (depth'[pi(v)] = depth[v] from pi(s)); the parent is not
+    invariant (the canonical pick is by id), but it is the oracle's either way."""
+    need_cuda()
+    scale = 13
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=313)
+    perm = np.random.default_rng(313).permutation(n).astype(np.int32)
+    og = oracle.Graph(n, src, dst)
+    og2 = oracle.Graph(n, perm[src], perm[dst])
+    g = gpu_graph(n, src, dst, th=32)
+    g2 = gpu_graph(n, perm[src], perm[dst], th=32)
+    mask = (np.diff(og.csr()[0]) > 0).astype(np.uint8)
+    for s in graphgen.sample_sources(mask, 8, seed=3131):
+        d, p = gpu_bfs(g, int(s))
+        d2, p2 = gpu_bfs(g2, int(perm[s]))
+        assert_same(d2[perm], d, "depth after relabelling (source %d)" % s)
+        assert_same(p2, og2.bfs(int(perm[s]))[1], "parent of the relabelled graph (source %d)" % s)
+
+
+@pytest.mark.parametrize("th", [5, 6, 7])
+def test_degree_exactly_th(th):
+    """A vertex of degree exactly TH stays normal, TH + 1 makes it a delegate
+    (strictly greater, Sec. III-A); results are the oracle's either way."""
+    need_cuda()
+    # hub 0 of degree 6 and hub 7 of degree 7 in a graph of 40 vertices
+    e = [(0, x) for x in range(1, 7)] + [(7, x) for x in range(8, 15)] + [(6, 8), (14, 20), (20, 21)]
+    e = np.asarray(e, np.int32)
+    n = 40
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th)
+    want_d = int(og.separate(th)[2])
+    assert g.info.delegates == want_d == (2 if th < 6 else (1 if th == 6 else 0))
+    for s in (0, 3, 7, 21, 30):
+        check_against_oracle(og, g, [s], stats=True, th=th)
