@@ -227,10 +227,11 @@ void bfs_batch_free(bfs_batch* b);
  * handles and owns a worker thread.  Submitted queries wait in one FIFO per
  * graph.  Whenever fewer than max_concurrent launches are in flight, the worker
  * takes the graph whose oldest waiting query arrived first and launches its
- * waiting queries on a stream of their own: a lone query runs the single-source
- * level loop (bfs_run's kernel, on the graph's run state, at most one such run
- * per graph at a time; with single_path = 1), several are packed, up to
- * max_lanes, into one multi-source launch (bfs_run_batch's kernel).  Either way a
+ * waiting queries on a stream of their own: when at most single_max are waiting
+ * they run back to back on the single-source level loop (bfs_run's kernel, on
+ * the graph's run state, one such launch per graph at a time; with single_path
+ * = 1), more are packed, up to max_lanes, into one multi-source launch
+ * (bfs_run_batch's kernel).  Either way a
  * query's result is its exact hop distance and canonical parent, the same as
  * alone.  Each query is reported when its launch ends.  Each launch gets capacity / max_concurrent CTAs, so all launches
  * in flight are co-resident.  Batch contexts are created on demand (at most
@@ -248,8 +249,10 @@ typedef struct bfs_server_options {
   int32_t contexts_per_graph; /* batch contexts per graph, 1..max_concurrent (0 = max_concurrent) */
   int64_t hbm_reserve_bytes;  /* device memory left free when a context is admitted */
   int64_t hbm_budget_bytes;   /* cap on the device bytes of all contexts held (0 = none) */
-  int32_t single_path;        /* 1: a lone query of a graph runs the single-source level loop */
-  int32_t reserved[7];        /* zero */
+  int32_t single_path;        /* 1: few waiting queries of a graph run the single-source level loop */
+  int32_t single_max;         /* at most this many waiting queries (1..4; 0 = 3) run back to back on
+                                 the level loop rather than as a batch */
+  int32_t reserved[6];        /* zero */
 } bfs_server_options;
 
 typedef struct bfs_server_done {

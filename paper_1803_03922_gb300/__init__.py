@@ -87,7 +87,7 @@ class bfs_batch_stats(ctypes.Structure):
 class bfs_server_options(ctypes.Structure):
     _fields_ = [("max_concurrent", c_i32), ("max_lanes", c_i32), ("with_parents", c_i32),
                 ("contexts_per_graph", c_i32), ("hbm_reserve_bytes", c_i64), ("hbm_budget_bytes", c_i64),
-                ("single_path", c_i32), ("reserved", c_i32 * 7)]
+                ("single_path", c_i32), ("single_max", c_i32), ("reserved", c_i32 * 6)]
 
 
 class bfs_server_done(ctypes.Structure):
@@ -487,7 +487,7 @@ class Server:
 
     def __init__(self, max_concurrent: int = 2, max_lanes: int = 64, with_parents: bool = True,
                  contexts_per_graph: int = 0, hbm_reserve_bytes: int = 0, hbm_budget_bytes: int = 0,
-                 single_path: bool = True):
+                 single_path: bool = True, single_max: int = 3):
         o = bfs_server_options_default()
         o.max_concurrent = max_concurrent
         o.max_lanes = max_lanes
@@ -496,6 +496,7 @@ class Server:
         o.hbm_reserve_bytes = hbm_reserve_bytes
         o.hbm_budget_bytes = hbm_budget_bytes
         o.single_path = 1 if single_path else 0
+        o.single_max = single_max
         self.with_parents = with_parents
         self.graphs = []
         self._live = {}  # ticket -> (depth, parent) kept alive until reported

@@ -10,9 +10,10 @@
 //
 // Scheduling: one FIFO per graph.  While fewer than max_concurrent launches run,
 // the graph whose oldest waiting query arrived first gets one launch of up to
-// max_lanes of its waiting queries: a lone query runs the single-source level
-// loop on the graph's own run state (when no other single run of that graph is
-// in flight), several share a multi-source batch on an idle batch context (or a
+// max_lanes of its waiting queries: when at most single_max are waiting they run
+// back to back on the single-source level loop on the graph's own run state
+// (when no other single run of that graph is in flight), more share a
+// multi-source batch on an idle batch context (or a
 // new one, if free device memory and the budget admit it, after freeing idle
 // contexts of other graphs least recently used first).  Every launch has
 // capacity / max_concurrent CTAs, so the cooperative launches in flight always
@@ -39,6 +40,7 @@ namespace {
 
 constexpr int kMaxLanes = 64;
 constexpr int kMaxConcurrent = 8;
+constexpr int kMaxSingle = 4;  // single-source runs per launch of a graph's level-loop context
 constexpr int64_t kStuckCheckNs = 1000000000;  // query a silent stream after 1 s
 
 int64_t now_ns() {
@@ -65,12 +67,12 @@ struct Context {
   bool single = false;     // runs the single-source level loop on the graph's run state
   bfs_batch* b = nullptr;  // batch contexts only
   cudaStream_t stream = nullptr;
-  RunHeader* hdr = nullptr;  // pinned host copy of the launch's run header
+  RunHeader* hdr = nullptr;  // pinned host copies of the launch's run headers [kMaxSingle]
   int64_t bytes = 0;
   bool busy = false;
   int64_t last_used = 0;
   std::vector<Query> q;  // the queries of the launch in flight
-  unsigned epoch = 0;
+  unsigned epoch[kMaxSingle] = {0, 0, 0, 0};
   int64_t t_launch = 0;
   std::atomic<int64_t> t_done{0};  // stamped by the stream's host function; 0 while running
 };
@@ -119,29 +121,35 @@ void CUDART_CB on_launch_done(void* arg) {  // runs on a CUDA thread: no CUDA ca
   s->cv_work.notify_one();
 }
 
-// Moves the queries of a finished (or failed) launch to the done list.
+// Moves the queries of a finished launch to the done list.  status: the launch's
+// own failure, or BFS_OK to take each query's status from its run header (one
+// header per single-source run, one for a whole batch).
 void finish(bfs_server* s, Context& c, int status, int64_t t_done) {
   const int k = (int)c.q.size();
-  const int levels = status == BFS_OK ? c.hdr->levels : 0;
-  const int64_t dev = status == BFS_OK ? (int64_t)(c.hdr->t1 - c.hdr->t0) : 0;
+  int failed = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    for (const Query& q : c.q) {
+    for (int i = 0; i < k; ++i) {
+      const Query& q = c.q[i];
+      const int hi = c.single ? i : 0;
+      const RunHeader& h = c.hdr[hi];
+      const int st = status != BFS_OK ? status : bfsgb::ms_header_status(h, c.epoch[hi]);
+      failed += st != BFS_OK;
       bfs_server_done d;
       std::memset(&d, 0, sizeof(d));
       d.ticket = q.ticket;
-      d.status = status;
+      d.status = st;
       d.graph_id = c.gid;
-      d.batch_size = k;
-      d.levels = levels;
+      d.batch_size = c.single ? 1 : k;
+      d.levels = st == BFS_OK ? h.levels : 0;
       d.t_arrival_ns = q.t_arrival;
       d.t_launch_ns = c.t_launch;
       d.t_done_ns = t_done;
-      d.device_ns = dev;
+      d.device_ns = st == BFS_OK ? (int64_t)(h.t1 - h.t0) : 0;
       s->done.push_back(d);
     }
     s->completed += k;
-    if (status != BFS_OK) s->failed += k;
+    s->failed += failed;
     s->in_flight -= 1;
   }
   c.q.clear();
@@ -157,7 +165,7 @@ void reap(bfs_server* s) {
     if (!c.busy) continue;
     const int64_t td = c.t_done.load(std::memory_order_acquire);
     if (td) {
-      finish(s, c, bfsgb::ms_header_status(*c.hdr, c.epoch), td);
+      finish(s, c, BFS_OK, td);
     } else if (now - c.t_launch > kStuckCheckNs) {
       // a stream whose work failed never runs its host function
       const cudaError_t e = cudaStreamQuery(c.stream);
@@ -199,12 +207,12 @@ Context* new_context(bfs_server* s, int gid) {
   c->srv = s;
   c->gid = gid;
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMallocHost((void**)&c->hdr, sizeof(RunHeader)) != cudaSuccess) {
+      cudaMallocHost((void**)&c->hdr, kMaxSingle * sizeof(RunHeader)) != cudaSuccess) {
     cudaGetLastError();
     if (c->stream) cudaStreamDestroy(c->stream);
     return nullptr;
   }
-  std::memset(c->hdr, 0, sizeof(RunHeader));
+  std::memset(c->hdr, 0, kMaxSingle * sizeof(RunHeader));
   s->ctx.push_back(std::move(c));
   return s->ctx.back().get();
 }
@@ -278,21 +286,26 @@ void launch(bfs_server* s, Context& c) {
       std::lock_guard<std::mutex> lk(s->mu);
       g = s->graphs[c.gid].g;
     }
-    rc = bfsgb::launch_run(g, src[0], nullptr, s->opt.with_parents ? pl[0] : nullptr, c.stream, s->slice, dl[0]);
-    c.epoch = g->epoch & 0x0FFFFFFFu;
-    if (rc == BFS_OK) {
-      const cudaError_t e = cudaMemcpyAsync(c.hdr, g->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, c.stream);
-      if (e != cudaSuccess) rc = cuda_fail(e, "copy run header");
+    // back-to-back runs on the graph's run state, each header copied after its run
+    rc = BFS_OK;
+    for (int i = 0; i < k && rc == BFS_OK; ++i) {
+      rc = bfsgb::launch_run(g, src[i], nullptr, s->opt.with_parents ? pl[i] : nullptr, c.stream, s->slice, dl[i]);
+      c.epoch[i] = g->epoch & 0x0FFFFFFFu;
+      if (rc == BFS_OK) {
+        const cudaError_t e =
+            cudaMemcpyAsync(c.hdr + i, g->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, c.stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "copy run header");
+      }
     }
   } else {
-    rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch);
+    rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch[0]);
   }
   if (rc == BFS_OK) {
     const cudaError_t e = cudaLaunchHostFunc(c.stream, on_launch_done, &c);
     if (e == cudaSuccess) return;
     rc = cuda_fail(e, "queue completion callback");
-    cudaStreamSynchronize(c.stream);
   }
+  cudaStreamSynchronize(c.stream);  // runs already queued finish before the context is reused
   finish(s, c, rc, now_ns());
 }
 
@@ -319,14 +332,14 @@ void schedule(bfs_server* s) {
         g = s->graphs[gid].g;
         waiting = s->graphs[gid].waiting.size();
       }
-      if (waiting == 1 && s->opt.single_path && (c = acquire_single(s, gid))) break;
+      if ((int)waiting <= s->opt.single_max && (c = acquire_single(s, gid))) break;
       if ((c = acquire_context(s, gid, g))) break;
     }
     if (!c) return;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       std::deque<Query>& w = s->graphs[c->gid].waiting;
-      const int cap = c->single ? 1 : s->opt.max_lanes;
+      const int cap = c->single ? s->opt.single_max : s->opt.max_lanes;
       while (!w.empty() && (int)c->q.size() < cap) {
         c->q.push_back(w.front());
         w.pop_front();
@@ -364,6 +377,7 @@ extern "C" void bfs_server_options_default(bfs_server_options* opt) {
   opt->with_parents = 1;
   opt->contexts_per_graph = 2;
   opt->single_path = 1;
+  opt->single_max = 3;
 }
 
 extern "C" int64_t bfs_server_now_ns(void) { return now_ns(); }
@@ -383,6 +397,9 @@ extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out
     return fail(BFS_ERR_INVALID, "contexts_per_graph must be 1..max_concurrent");
   if (o.with_parents != 0 && o.with_parents != 1) return fail(BFS_ERR_INVALID, "with_parents must be 0 or 1");
   if (o.single_path != 0 && o.single_path != 1) return fail(BFS_ERR_INVALID, "single_path must be 0 or 1");
+  if (o.single_max < 0 || o.single_max > kMaxSingle) return fail(BFS_ERR_INVALID, "single_max must be 0..4");
+  if (!o.single_path) o.single_max = 0;
+  else if (o.single_max == 0) o.single_max = 3;
   if (o.hbm_reserve_bytes < 0 || o.hbm_budget_bytes < 0) return fail(BFS_ERR_INVALID, "byte limits must be >= 0");
   int dev = 0, cap = 0;
   const cudaError_t e = cudaGetDevice(&dev);

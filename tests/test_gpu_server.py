@@ -197,6 +197,12 @@ def test_lone_queries_and_depth_overflow(single_path):
     _check_oracle(ogs, q, recs)
     st = srv.stats()
     assert st["single_launches"] == (30 if single_path else 0)
+    # a few queries of one graph at once: back to back on the level loop while
+    # that graph's single-source state is free, else as a batch
+    q3 = [(1, int(x)) for x in np.random.default_rng(43).integers(0, gs[1].n, 3)]
+    recs3 = _run_mix(srv, q3)
+    _check_oracle(ogs, q3, recs3)
+    assert (srv.stats()["single_launches"] > 30) == single_path
     e = np.array([(i, i + 1) for i in range(299)], np.int32)  # depth 299 from an end
     deep = gpu_graph(300, e[:, 0], e[:, 1], th=8)
     gid = srv.add_graph(deep)
