@@ -69,6 +69,7 @@ struct Context {
   cudaStream_t stream = nullptr;
   RunHeader* hdr = nullptr;  // pinned host copies of the launch's run headers [kMaxSingle]
   int64_t bytes = 0;
+  int ctas = 0;  // CTAs of the launch in flight
   bool busy = false;
   int64_t last_used = 0;
   std::vector<Query> q;  // the queries of the launch in flight
@@ -105,6 +106,7 @@ struct bfs_server {
   int64_t created = 0, evicted = 0, ctx_bytes = 0;
   // worker thread only
   std::vector<std::unique_ptr<Context>> ctx;
+  int ctas_in_use = 0;
   std::thread worker;
 };
 
@@ -155,6 +157,8 @@ void finish(bfs_server* s, Context& c, int status, int64_t t_done) {
   c.q.clear();
   c.busy = false;
   c.last_used = t_done;
+  s->ctas_in_use -= c.ctas;
+  c.ctas = 0;
   s->cv_done.notify_all();
 }
 
@@ -289,7 +293,7 @@ void launch(bfs_server* s, Context& c) {
     // back-to-back runs on the graph's run state, each header copied after its run
     rc = BFS_OK;
     for (int i = 0; i < k && rc == BFS_OK; ++i) {
-      rc = bfsgb::launch_run(g, src[i], nullptr, s->opt.with_parents ? pl[i] : nullptr, c.stream, s->slice, dl[i]);
+      rc = bfsgb::launch_run(g, src[i], nullptr, s->opt.with_parents ? pl[i] : nullptr, c.stream, c.ctas, dl[i]);
       c.epoch[i] = g->epoch & 0x0FFFFFFFu;
       if (rc == BFS_OK) {
         const cudaError_t e =
@@ -323,7 +327,11 @@ void schedule(bfs_server* s) {
         return qa.t_arrival != qb.t_arrival ? qa.t_arrival < qb.t_arrival : qa.ticket < qb.ticket;
       });
     }
+    // CTAs: a batch takes its slice; single-source runs take the whole device when
+    // nothing else runs, else a slice; launches start only while they all fit
+    const int free_ctas = s->capacity - s->ctas_in_use;
     Context* c = nullptr;
+    int ctas = 0;
     for (int gid : order) {
       const bfs_graph* g;
       size_t waiting;
@@ -332,10 +340,19 @@ void schedule(bfs_server* s) {
         g = s->graphs[gid].g;
         waiting = s->graphs[gid].waiting.size();
       }
-      if ((int)waiting <= s->opt.single_max && (c = acquire_single(s, gid))) break;
-      if ((c = acquire_context(s, gid, g))) break;
+      if (free_ctas < s->slice) break;
+      if ((int)waiting <= s->opt.single_max && (c = acquire_single(s, gid))) {
+        ctas = s->ctas_in_use == 0 ? s->capacity : s->slice;
+        break;
+      }
+      if ((c = acquire_context(s, gid, g))) {
+        ctas = s->slice;
+        break;
+      }
     }
     if (!c) return;
+    c->ctas = ctas;
+    s->ctas_in_use += ctas;
     {
       std::lock_guard<std::mutex> lk(s->mu);
       std::deque<Query>& w = s->graphs[c->gid].waiting;
