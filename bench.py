@@ -673,6 +673,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--serving-only", action="store_true", help="print only the batched and serving measurements")
+    ap.add_argument("--batched-only", metavar="GRAPH", choices=sorted(WORKLOADS),
+                    help="print only the 64-lane batched measurement on GRAPH")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     w = WORKLOADS[args.workload]
@@ -685,6 +687,11 @@ def main():
     torch.cuda.set_device(local)
     if args.serving_only:
         print(json.dumps(serving_extras(torch.cuda.current_stream())), flush=True)
+        return
+    if args.batched_only:
+        g, srcs = build_served_graph(WORKLOADS[args.batched_only])
+        print(json.dumps({args.batched_only: batched_vs_single(g, srcs)}), flush=True)
+        g.close()
         return
     if ws > 1:
         import torch.distributed as dist
