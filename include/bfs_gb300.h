@@ -71,7 +71,9 @@ typedef struct bfs_options {
   int32_t test_skip_barrier;  /* testing only: CTA 0 leaves before the first grid barrier, so the
                                  other CTAs' bounded wait expires and the run reports BFS_ERR_TIMEOUT */
   int32_t run_timeout_ms;     /* bound of one run's device time (default 60000): BFS_ERR_TIMEOUT */
-  int32_t tuning;             /* bit 0: forward visits read the discovered word before an atomicOr */
+  int32_t tuning;             /* bit 0: forward visits read the discovered word before an atomicOr;
+                                 bit 1: record when the first and the last CTA finish each
+                                 expansion (bfs_level_log t_first_done_ns / t_last_done_ns) */
   int32_t reserved[4];
 } bfs_options;
 
@@ -135,7 +137,8 @@ typedef struct bfs_level_log {
   int64_t found;          /* |F_{L+1}| */
   int64_t queue_entries;  /* normal-vertex queue entries holding F_L (forward levels) */
   uint64_t t_begin_ns, t_expand_ns, t_end_ns; /* device %globaltimer at the phase edges */
-  uint64_t t_first_done_ns, t_last_done_ns;   /* when the first / last CTA finished the expansion */
+  uint64_t t_first_done_ns, t_last_done_ns;   /* when the first / last CTA finished the expansion
+                                                 (with tuning bit 1; else 0) */
 } bfs_level_log;
 
 typedef struct bfs_stats {
