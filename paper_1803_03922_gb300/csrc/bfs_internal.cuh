@@ -16,7 +16,7 @@ constexpr int kMaxWarpsPerBlock = 32;  // shared arrays indexed by warp fit 1024
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
 constexpr int kHead = 4;              // row entries kept in the per-vertex head record
-constexpr int64_t kShort = 64;        // rows with more entries left after the head go to the long-row path
+constexpr int64_t kShort = 1024;      // rows with more entries left after the head go to the long-row path
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxBlocks = 2048;      // upper bound of the level-loop grid (arrival words)
 

@@ -268,3 +268,19 @@ def test_degree_exactly_th(th):
     assert g.info.delegates == want_d == (2 if th < 6 else (1 if th == 6 else 0))
     for s in (0, 3, 7, 21, 30):
         check_against_oracle(og, g, [s], stats=True, th=th)
+
+
+@pytest.mark.parametrize("th", [16, 4000])
+def test_long_row_drain(th):
+    """Backward levels hand rows that settle nothing in their first entries to a
+    list drained by all warps: hub 0 (leaves 1..3000) finds its only frontier
+    neighbour at row position 2998, past the per-lane scan; results and counters
+    are the oracle's (forced backward from level 1)."""
+    need_cuda()
+    n_leaf = 3000
+    e = [(0, x) for x in range(1, n_leaf + 1)] + [(n_leaf + 1, n_leaf - 1), (n_leaf + 2, 5)]
+    e = np.asarray(e, np.int32)
+    n = n_leaf + 10
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th, schedule=2)
+    check_against_oracle(og, g, [n_leaf + 1, n_leaf + 2, 0, 7], stats=True, th=th)
