@@ -310,13 +310,19 @@ def cpu_oracle_sample(w, host_edges, sources, ce_dev, budget_s=20.0, max_sources
 
 def host_cpu():
     """The host's CPU model and logical core count (the CPU baseline runs on one)."""
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+                 "0xd49": "Arm Neoverse N2"}
     model = platform.machine()
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key = line.split(":", 1)[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware"):
-                    model = line.split(":", 1)[1].strip() or model
+                value = line.split(":", 1)[1].strip() if ":" in line else ""
+                if key == "model name" and value:
+                    model = value
+                    break
+                if key == "cpu part" and value:
+                    model = "%s (part %s)" % (arm_parts.get(value, "Arm"), value)
                     break
     except OSError:
         pass
