@@ -425,17 +425,24 @@ def build_served_graph(w):
 
 def batched_vs_single(g, sources, batches=8):
     """64-lane batches against one query at a time on the same graph and sources:
-    queries/s from CUDA events over `batches` x 64 queries, parents included."""
+    queries/s from CUDA events over `batches` x 64 queries, parents included, and
+    the aggregate GTEPS (the queries' traversed component edges / time)."""
     import torch
 
     import paper_1803_03922_gb300 as bfs
 
     n = g.n
     out = {}
+    edges = None  # traversed component edges of the timed batches' queries (untimed stats runs)
     for with_par in (True, False):
         b = bfs.Batch(g, with_parents=with_par)
         depth = torch.empty((64, n), dtype=torch.uint8, device="cuda")
         parent = torch.empty((64, n), dtype=torch.int32, device="cuda") if with_par else None
+        if edges is None:
+            edges = 0
+            for i in range(batches):
+                _, _, st = b.run(sources[64 * i:64 * (i + 1)], depth, parent, stats=True)
+                edges += st.traversed_edges
         for i in range(2):
             b.run(sources[64 * i:64 * (i + 1)], depth, parent)
         torch.cuda.synchronize()
@@ -449,6 +456,7 @@ def batched_vs_single(g, sources, batches=8):
         ms = e0.elapsed_time(e1)
         out["batched_qps" if with_par else "batched_depth_only_qps"] = 64 * batches / ms * 1e3
         out["ms_per_batch" if with_par else "ms_per_batch_depth_only"] = ms / batches
+        out["gteps_aggregate" if with_par else "gteps_aggregate_depth_only"] = edges / (ms / 1e3) / 1e9
         b.close()
         del depth, parent
         torch.cuda.empty_cache()
@@ -466,6 +474,7 @@ def batched_vs_single(g, sources, batches=8):
     g.wait()
     ms = e0.elapsed_time(e1)
     out["single_qps"] = 64 * batches / ms * 1e3
+    out["single_gteps_aggregate"] = edges / (ms / 1e3) / 1e9
     out["speedup"] = out["batched_qps"] / out["single_qps"]
     return out
 
