@@ -389,7 +389,7 @@ __device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, i
   const int32_t* Qc = (L & 1) ? p.Q1 : p.Q0;
   const int2* CLc = (L & 1) ? p.CL1 : p.CL0;
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = gwarp; it < total; it += nwarps) {
     if (it < nch)
@@ -524,7 +524,7 @@ __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, u
   found[lane] = 0u;
   __syncwarp();
   const int64_t W = p.words;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t nitems = (W + iw - 1) / iw;
@@ -544,7 +544,7 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
   uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
   const long long nl = (long long)__ldcg(&sc->nlong);
   if (nl == 0) return;
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   WorkCursor wc(nl, gwarp, nwarps, &sc->work2);
   for (long long e = wc.next(); e < nl; e = wc.next()) {
@@ -584,7 +584,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
                                      bool count, int depth, Acc& acc) {
   const int64_t W = p.words;
   const int lane = lane_id();
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   // the delegate prefix is dense in new vertices after a forward level: items of
   // two words there, 32 words elsewhere
@@ -689,7 +689,7 @@ __device__ void pull_parents(const BfsParams& p, const uint32_t* __restrict__ Vc
   const int32_t* Qn = (L & 1) ? p.Q0 : p.Q1;
   const int2* CLn = (L & 1) ? p.CL0 : p.CL1;
   const int lane = lane_id();
-  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t b = gwarp; b * 32 < qn; b += nwarps) {
     const int64_t i = b * 32 + lane;

@@ -128,6 +128,13 @@ __device__ int grid_sync(const P& p, unsigned& seq, F&& master, int flags = 0) {
 
 __device__ __forceinline__ int no_master(int) { return 0; }
 
+// A warp's index for static work splits, numbered CTA-interleaved (warp 0 of
+// every CTA first, then warp 1, ...), so that a level with fewer items than warps
+// spreads them over all SMs instead of filling the first CTAs.
+__device__ __forceinline__ int64_t spread_warp() {
+  return (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+}
+
 
 // Exclusive prefix sum over the CTA of two per-thread counts; returns the
 // CTA totals.  Called by all threads of the CTA.
