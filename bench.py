@@ -476,6 +476,29 @@ def batched_vs_single(g, sources, batches=8):
     out["single_qps"] = 64 * batches / ms * 1e3
     out["single_gteps_aggregate"] = edges / (ms / 1e3) / 1e9
     out["speedup"] = out["batched_qps"] / out["single_qps"]
+    # the batched schedule autotuned (Beamer alpha of the union frontier), then timed as above
+    from paper_1803_03922_gb300.autotune import tune_batch_alpha
+
+    alpha0 = g.opt.alpha
+    best, cand = tune_batch_alpha(g, sources, batches=2)
+    b = bfs.Batch(g, with_parents=True)
+    depth = torch.empty((64, n), dtype=torch.uint8, device="cuda")
+    parent = torch.empty((64, n), dtype=torch.int32, device="cuda")
+    b.run(sources[:64], depth, parent)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(batches):
+        b.run(sources[64 * i:64 * (i + 1)], depth, parent)
+    e1.record()
+    torch.cuda.synchronize()
+    b.wait()
+    ms = e0.elapsed_time(e1)
+    out["autotuned_alpha"] = best
+    out["autotuned_batched_qps"] = 64 * batches / ms * 1e3
+    out["autotuned_candidates_ms_per_batch"] = {str(a): round(t * 1e3, 3) for a, t in cand.items()}
+    b.close()
+    g.set_options(alpha=alpha0)
     return out
 
 

@@ -198,3 +198,39 @@ def device_tuner(src, dst, n: int, sources: Sequence[int], runs: int = 2, ths: I
         if th != res.th:
             g.close()
     return res, best
+
+
+BATCH_ALPHA = (2, 5, 15, 30, 60, 120)
+
+
+def tune_batch_alpha(graph, sources, alphas: Iterable[int] = BATCH_ALPHA, batches: int = 2,
+                     with_parents: bool = True) -> Tuple[int, Dict[int, float]]:
+    """Schedule of the 64-lane batched form: its direction rule is Beamer's alpha on
+    the union frontier (once backward, it stays backward), so the search is over
+    alpha.  Times `batches` batches of 64 of `sources` per candidate on the device;
+    returns the best alpha and the seconds per batch of every candidate.  The
+    graph's alpha is left at the best value."""
+    import torch
+
+    from . import Batch
+
+    b = Batch(graph, with_parents=with_parents)
+    n = graph.n
+    depth = torch.empty((64, n), dtype=torch.uint8, device="cuda")
+    parent = torch.empty((64, n), dtype=torch.int32, device="cuda") if with_parents else None
+    times = {}
+    for a in alphas:
+        graph.set_options(alpha=int(a))
+        b.run(sources[:64], depth, parent)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(batches):
+            b.run(sources[64 * i:64 * (i + 1)], depth, parent)
+        e1.record()
+        torch.cuda.synchronize()
+        b.wait()
+        times[int(a)] = e0.elapsed_time(e1) / 1e3 / batches
+    best = min(times, key=times.get)
+    graph.set_options(alpha=best)
+    b.close()
+    return best, times

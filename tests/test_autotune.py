@@ -76,3 +76,34 @@ def test_th_rule_per_scale():
     assert 16 in th_space_for_scale(26) and 8 in th_space_for_scale(26) and 32 in th_space_for_scale(26)
     row = {"delegates": 10, "nn_pct": 12.0}
     assert th_goals(row, 100) == {"delegates_under_4n_over_p": True, "nn_under_10pct": False}
+
+
+@pytest.mark.gpu
+def test_batch_alpha_tuning_keeps_results():
+    """The batched form's schedule search (alpha of the union frontier) leaves the
+    graph at the best alpha; every query still gets the oracle's result."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import numpy as np
+
+    import graphgen
+    import oracle
+    import paper_1803_03922_gb300 as bfs
+    from paper_1803_03922_gb300.autotune import tune_batch_alpha
+
+    scale = 13
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=413)
+    og = oracle.Graph(n, src, dst)
+    g = bfs.Graph(np.ascontiguousarray(src), np.ascontiguousarray(dst), n, th=32)
+    mask = (np.diff(og.csr()[0]) > 0).astype(np.uint8)
+    sources = graphgen.sample_sources(mask, 128, seed=4131)
+    best, times = tune_batch_alpha(g, sources, alphas=(2, 15, 120), batches=2)
+    assert best in times and g.opt.alpha == best and len(times) == 3
+    b = bfs.Batch(g)
+    d, p = b.run(sources[:64])
+    want_d, want_p = og.bfs_batch_u8(sources[:64])
+    assert np.array_equal(d.cpu().numpy(), want_d) and np.array_equal(p.cpu().numpy(), want_p)
+    b.close()
+    g.close()
