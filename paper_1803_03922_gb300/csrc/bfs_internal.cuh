@@ -16,7 +16,9 @@ constexpr int kMaxWarpsPerBlock = 32;  // shared arrays indexed by warp fit 1024
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
 constexpr int kHead = 4;              // row entries kept in the per-vertex head record
-constexpr int64_t kShort = 1024;      // rows with more entries left after the head go to the long-row path
+constexpr int64_t kShort = 4096;      // rows with more entries left after the head go to the long-row path
+constexpr int kTailLanes = 4;         // lanes per row in the short-row group scan of a pull (2, 4, 8 or 16)
+constexpr int kTailPerLane = 4;       // row entries per lane and step there (1, or 2 / 4 as one 64- / 128-bit load)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxBlocks = 2048;      // upper bound of the level-loop grid (arrival words)
 

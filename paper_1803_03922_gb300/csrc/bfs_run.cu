@@ -99,8 +99,10 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
 
 // Phases B and C of a pull scan: lanes with `more` have scanned the first
 // kHead entries of their row [beg,end) without a hit.
-//  B: rows with at most kShort entries left go to 8-lane groups, four rows at a
-//     time, one 32-byte sector per group and step;
+//  B: rows with at most kShort entries left go to groups of kTailLanes (4)
+//     lanes, eight rows at a time; each lane loads kTailPerLane (4) entries with
+//     one 128-bit load, so a group reads 16 entries (64 bytes) per step, from a
+//     4-entry boundary with the entries before the tail masked;
 //  C: longer rows are finished by the whole warp, one row at a time, 128 entries
 //     per step.
 // On a hit, hit/k are set (k = first-hit position + 1); otherwise k = end - beg.
@@ -111,36 +113,71 @@ constexpr int kDeferred = -2;
 template <bool kFix>
 __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t end, const uint32_t* __restrict__ Ncur,
                           int& hit, int64_t& k, int defer_v = -1, LevelSlot* defer_slot = nullptr) {
+  constexpr int G = kTailLanes, P = kTailPerLane, R = 32 / G, S = G * P;
+  static_assert(G == 2 || G == 4 || G == 8 || G == 16, "group scan: 2, 4, 8 or 16 lanes per row");
+  static_assert(P == 1 || P == 2 || P == 4, "group scan: 1 entry, or one 64- or 128-bit load per lane");
+  constexpr unsigned kGroupMask = (1u << G) - 1u;
   const int lane = lane_id();
   if (more) k = end - beg;
   const bool longrow = more && (end - beg - kHead) > kShort;
   unsigned rem = __ballot_sync(kFull, more && !longrow);
-  const int g = lane >> 3, sub = lane & 7;
+  const int g = lane / G, sub = lane % G;
   while (rem) {
-    const int take = min(__popc(rem), 4);
+    const int take = min(__popc(rem), R);
     unsigned r = rem;
-    for (int q = 0; q < g && q < 3; ++q) r &= r - 1;
+    for (int q = 0; q < g && q < R - 1; ++q) r &= r - 1;
     const int srcl = (g < take) ? (__ffs(r) - 1) : 0;
     const int64_t rbeg = __shfl_sync(kFull, beg, srcl);
     const int64_t rend = __shfl_sync(kFull, end, srcl);
+    const int64_t from = rbeg + kHead;
     bool gdone = g >= take;
     int ghit = -1;
     int64_t gk = 0;
-    int64_t pos = rbeg + kHead;
+    // with 128-bit loads a step starts on a 4-entry boundary; entries before
+    // `from` are masked
+    int64_t pos = from & ~(int64_t)(P - 1);
     while (__any_sync(kFull, !gdone)) {
-      const int64_t j = pos + sub;
-      const int c = (!gdone && j < rend) ? p.col[j] : -1;
-      const bool h = c >= 0 && probe<kFix>(p, c, Ncur);
-      const unsigned gb = (__ballot_sync(kFull, h) >> (g * 8)) & 0xFFu;
+      const int64_t j = pos + sub * P;
+      int c = -1, t0 = 0;  // this lane's first passing entry and its offset in the lane's P entries
+      if (!gdone && j < rend) {
+        if constexpr (P == 1) {
+          const int c1 = p.col[j];
+          if (probe<kFix>(p, c1, Ncur)) c = c1;
+        } else {
+          int cs[P];
+          if constexpr (P == 4) {
+            const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
+            cs[0] = c4.x;
+            cs[1] = c4.y;
+            cs[2] = c4.z;
+            cs[3] = c4.w;
+          } else {
+            const int2 c2 = __ldg(reinterpret_cast<const int2*>(p.col + j));
+            cs[0] = c2.x;
+            cs[1] = c2.y;
+          }
+          bool hh[P];
+#pragma unroll
+          for (int t = 0; t < P; ++t) hh[t] = j + t >= from && j + t < rend && probe<kFix>(p, cs[t], Ncur);
+#pragma unroll
+          for (int t = P - 1; t >= 0; --t)
+            if (hh[t]) {
+              c = cs[t];
+              t0 = t;
+            }
+        }
+      }
+      const unsigned gb = (__ballot_sync(kFull, c >= 0) >> (g * G)) & kGroupMask;
       const int first = gb ? __ffs(gb) - 1 : 0;
-      const int hc = __shfl_sync(kFull, c, g * 8 + first);
+      const int hc = __shfl_sync(kFull, c, g * G + first);
+      const int ht = P == 1 ? 0 : __shfl_sync(kFull, t0, g * G + first);
       if (!gdone) {
         if (gb) {
           ghit = hc;
-          gk = pos + first - rbeg + 1;
+          gk = pos + first * P + ht - rbeg + 1;
           gdone = true;
         } else {
-          pos += 8;
+          pos += S;
           if (pos >= rend) {
             gdone = true;
             gk = rend - rbeg;
@@ -149,10 +186,10 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
       }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int h2 = __shfl_sync(kFull, ghit, q * 8);
-      const int64_t k2 = __shfl_sync(kFull, gk, q * 8);
-      const int owner = __shfl_sync(kFull, srcl, q * 8);
+    for (int q = 0; q < R; ++q) {
+      const int h2 = __shfl_sync(kFull, ghit, q * G);
+      const int64_t k2 = __shfl_sync(kFull, gk, q * G);
+      const int owner = __shfl_sync(kFull, srcl, q * G);
       if (q < take && lane == owner) {
         hit = h2;
         k = k2;

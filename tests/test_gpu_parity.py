@@ -273,14 +273,40 @@ def test_degree_exactly_th(th):
 @pytest.mark.parametrize("th", [16, 4000])
 def test_long_row_drain(th):
     """Backward levels hand rows that settle nothing in their first entries to a
-    list drained by all warps: hub 0 (leaves 1..3000) finds its only frontier
-    neighbour at row position 2998, past the per-lane scan; results and counters
-    are the oracle's (forced backward from level 1)."""
+    list drained by all warps: hub 0 (leaves 1..10000) finds its only frontier
+    neighbour at row position 9998, past the short-row group scan; results and
+    counters are the oracle's (forced backward from level 1)."""
     need_cuda()
-    n_leaf = 3000
+    n_leaf = 10000
     e = [(0, x) for x in range(1, n_leaf + 1)] + [(n_leaf + 1, n_leaf - 1), (n_leaf + 2, 5)]
     e = np.asarray(e, np.int32)
     n = n_leaf + 10
     og = oracle.Graph(n, e[:, 0], e[:, 1])
     g = gpu_graph(n, e[:, 0], e[:, 1], th=th, schedule=2)
     check_against_oracle(og, g, [n_leaf + 1, n_leaf + 2, 0, 7], stats=True, th=th)
+
+
+@pytest.mark.parametrize("th", [16, 4000])
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_group_scan_hit_positions(th, shift):
+    """A backward scan past the head entries reads a short row in aligned 4-entry
+    loads: the hub's only frontier neighbour sits at every position class of the
+    row (head, the first masked load, 4-entry and 16-entry boundaries, the last
+    entry), and `shift` extra entries in a lower row move the hub's row start off
+    the 4-entry grid (with TH 4000 the hub is a normal vertex and keeps its place).
+    Depth, parent and the examined-entry counters equal the oracle's."""
+    need_cuda()
+    n_leaf, hub = 70, 10
+    leaves = list(range(hub + 1, hub + 1 + n_leaf))
+    e = [(hub, x) for x in leaves] + [(i, leaves[-1]) for i in range(shift)]
+    positions = [0, 1, 3, 4, 5, 6, 7, 8, 15, 16, 19, 20, 21, 35, 36, 52, n_leaf - 1]
+    sources = []
+    for j, pos in enumerate(positions):
+        s_j = hub + 1 + n_leaf + j
+        e.append((s_j, leaves[pos]))
+        sources.append(s_j)
+    e = np.asarray(e, np.int32)
+    n = hub + 1 + n_leaf + len(positions)
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th, schedule=2)
+    check_against_oracle(og, g, sources, stats=True, th=th)
