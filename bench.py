@@ -217,6 +217,9 @@ class DeviceWorkload:
         self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
         # untimed pass: per-source traversal size, byte model and level log
         self.ce, self.model, self.levels, self.dirs, self.phase = [], [], [], [], []
+        # per phase: [model bytes, device ns] summed over the sources (level log)
+        self.phases = {"forward_expand": [0, 0], "forward_level_end": [0, 0], "backward_level": [0, 0]}
+        bm = 4 * ((self.info.n_nonisolated + 31) // 32)  # one pass over a bitmap
         for s in self.sources:
             _, _, st = self.g.run(int(s), self.depth, self.parent, stats=True)
             self.ce.append(st.component_edges)
@@ -229,9 +232,27 @@ class DeviceWorkload:
                 dt = lv.t_end_ns - lv.t_begin_ns
                 if lv.direction:
                     bu += dt
+                    ph = self.phases["backward_level"]
+                    ph[0] += 5 * bm + 8 * lv.scanned + 8 * lv.edges_examined + 12 * lv.found
+                    ph[1] += dt
                 else:
                     td += dt
+                    ph = self.phases["forward_expand"]
+                    ph[0] += 20 * lv.frontier + 8 * lv.frontier_edges
+                    ph[1] += lv.t_expand_ns - lv.t_begin_ns
+                    ph = self.phases["forward_level_end"]
+                    ph[0] += 4 * bm + 12 * lv.found
+                    ph[1] += lv.t_end_ns - lv.t_expand_ns
             self.phase.append((td, bu, st.device_ns))
+
+    def phase_roofline(self, peak):
+        """Model bytes / device time of each phase over all sources (device timer of
+        the level log; each phase's time ends at the grid barrier that closes it)."""
+        out = {}
+        for k, (b, ns) in self.phases.items():
+            if ns > 0:
+                out[k] = {"model_gb": b / 1e9, "ms": ns / 1e6, "achieved_gbs": b / ns, "frac": b / ns / peak}
+        return out
 
     def timed(self, steps, flush, stream):
         """steps x len(sources) runs; returns per-run device seconds (CUDA events)."""
@@ -796,6 +817,7 @@ def main():
                    "directions_first_source": dw.dirs[0],
                    "forward_share": td_ns / dev_ns if dev_ns else None,
                    "backward_share": bu_ns / dev_ns if dev_ns else None,
+                   "phase_roofline": dw.phase_roofline(peak),
                    "e2e_ms_per_bfs_median": 1e3 * statistics.median(e2e_ts)},
     }
     host_edges = dw.host_edges
@@ -846,7 +868,8 @@ def main():
                                 / sum(t3) / 1e9 / peak,
                                 "nnz": d3.info.nnz, "delegates": d3.info.delegates,
                                 "levels": statistics.median(d3.levels), "build_s": d3.build_s,
-                                "directions_first_source": d3.dirs[0]}
+                                "directions_first_source": d3.dirs[0],
+                                "phase_roofline": d3.phase_roofline(peak)}
                 if key == "rmat26":
                     extras["degree_classes_rmat26"] = degree_table(d3.g.degree_classes(DEGREE_THS))
                 d3.close()
