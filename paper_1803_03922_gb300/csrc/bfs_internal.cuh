@@ -16,6 +16,8 @@ constexpr int kMaxWarpsPerBlock = 32;  // shared arrays indexed by warp fit 1024
 constexpr int64_t kChunk = 512;       // row entries per delegate work item in a forward level
 constexpr int kColPad = 32;           // int32 slack after the last column (128-bit over-reads)
 constexpr int kHead = 4;              // row entries kept in the per-vertex head record
+constexpr int kHeadVecs = kHead / 2;  // int4 words per head record: kHead ids, then kHead caller ids
+static_assert(kHead == 2 || kHead == 4 || kHead == 8, "head records hold 2, 4 or 8 entries");
 constexpr int64_t kShort = 4096;      // rows with more entries left after the head go to the long-row path
 constexpr int kTailLanes = 4;         // lanes per row in the short-row group scan of a pull (2, 4, 8 or 16)
 constexpr int kTailPerLane = 4;       // row entries per lane and step there (1, or 2 / 4 as one 64- / 128-bit load)
@@ -64,7 +66,7 @@ struct BfsParams {
   const int32_t* col;        // [nnz + kColPad]
   const int32_t* caller_of;  // [n]
   const int32_t* internal_of;// [n]
-  const int4* head;          // [2 n_ni]: first kHead neighbours (internal ids, -1 pad), then their caller ids
+  const int4* head;          // [kHeadVecs n_ni]: first kHead neighbours (internal ids, -1 pad), then their caller ids
   const int32_t* deg;        // [n_ni] degree
   uint32_t* V;               // visited bitmaps, [words] each: level L reads one and writes
   uint32_t* V1;              // the other (depth <= L and depth <= L+1)

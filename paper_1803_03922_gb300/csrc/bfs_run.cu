@@ -227,18 +227,37 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
 // degree.  Split from the probes so a caller can put several vertices' loads in
 // flight before the first probe.
 struct HeadRec {
-  int4 nb, cid;
+  int nb[kHead], cid[kHead];
   int deg;
 };
 
 __device__ __forceinline__ HeadRec head_load(const BfsParams& p, bool act, int v) {
   HeadRec h;
-  h.nb = make_int4(-1, -1, -1, -1);
-  h.cid = h.nb;
+#pragma unroll
+  for (int t = 0; t < kHead; ++t) h.nb[t] = h.cid[t] = -1;
   h.deg = 0;
   if (act) {
-    h.nb = __ldg(p.head + 2 * (int64_t)v);
-    h.cid = __ldg(p.head + 2 * (int64_t)v + 1);
+    if constexpr (kHead >= 4) {
+#pragma unroll
+      for (int t = 0; t < kHead; t += 4) {
+        const int4 a = __ldg(p.head + kHeadVecs * (int64_t)v + t / 4);
+        const int4 b = __ldg(p.head + kHeadVecs * (int64_t)v + kHead / 4 + t / 4);
+        h.nb[t] = a.x;
+        h.nb[t + 1] = a.y;
+        h.nb[t + 2] = a.z;
+        h.nb[t + 3] = a.w;
+        h.cid[t] = b.x;
+        h.cid[t + 1] = b.y;
+        h.cid[t + 2] = b.z;
+        h.cid[t + 3] = b.w;
+      }
+    } else {
+      const int4 a = __ldg(p.head + (int64_t)v);
+      h.nb[0] = a.x;
+      h.nb[1] = a.y;
+      h.cid[0] = a.z;
+      h.cid[1] = a.w;
+    }
     h.deg = __ldg(p.deg + v);
   }
   return h;
@@ -249,8 +268,8 @@ __device__ __forceinline__ HeadRec head_load(const BfsParams& p, bool act, int v
 template <bool kFix>
 __device__ __forceinline__ void head_probe(const BfsParams& p, const HeadRec& h, const uint32_t* __restrict__ Ncur,
                                            int& hit, int& cid, int64_t& k) {
-  const int nb[kHead] = {h.nb.x, h.nb.y, h.nb.z, h.nb.w};
-  const int cs[kHead] = {h.cid.x, h.cid.y, h.cid.z, h.cid.w};
+  const int* nb = h.nb;
+  const int* cs = h.cid;
   bool hh[kHead];
 #pragma unroll
   for (int t = 0; t < kHead; ++t) hh[t] = nb[t] >= 0 && probe<kFix>(p, nb[t], Ncur);

@@ -127,8 +127,8 @@ __global__ void k_degree_stats(const int64_t* __restrict__ off, int32_t n_ni, in
 }
 
 // Per-vertex head record: the first kHead row entries (internal ids, -1 past the
-// end) and their caller ids, one 32-byte sector per vertex, plus an int32 degree
-// array.  A backward scan that settles within the first entries reads only this
+// end) and their caller ids (with kHead = 4 one 32-byte sector per vertex; with
+// 2 the four ints share one 16-byte word), plus an int32 degree array.  A backward scan that settles within the first entries reads only this
 // sector, indexed by the vertex itself (coalesced across a warp).
 __global__ void k_heads(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                         const int32_t* __restrict__ caller_of, int32_t n_ni, int4* __restrict__ head,
@@ -141,8 +141,15 @@ __global__ void k_heads(const int64_t* __restrict__ off, const int32_t* __restri
       nb[t] = (b + t < e) ? col[b + t] : -1;
       cid[t] = nb[t] >= 0 ? caller_of[nb[t]] : -1;
     }
-    head[2 * v] = make_int4(nb[0], nb[1], nb[2], nb[3]);
-    head[2 * v + 1] = make_int4(cid[0], cid[1], cid[2], cid[3]);
+    if constexpr (kHead == 2) {
+      head[v] = make_int4(nb[0], nb[1], cid[0], cid[1]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < kHead; t += 4) {
+        head[kHeadVecs * v + t / 4] = make_int4(nb[t], nb[t + 1], nb[t + 2], nb[t + 3]);
+        head[kHeadVecs * v + kHead / 4 + t / 4] = make_int4(cid[t], cid[t + 1], cid[t + 2], cid[t + 3]);
+      }
+    }
     deg[v] = (int32_t)(e - b);
   }
 }
@@ -322,9 +329,9 @@ int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, co
   if (M > 0)
     k_scatter_cols<<<grid_for(M), kB, 0, s>>>(ka.as<uint64_t>(), M, start_c.as<int64_t>(), g->internal_of, g->off,
                                               g->d, g->col, sub.as<unsigned long long>());
-  BFS_CUDA(cudaMalloc(&g->head, ((size_t)g->n_ni + 1) * 2 * sizeof(int4)), "alloc head records");
+  BFS_CUDA(cudaMalloc(&g->head, ((size_t)g->n_ni + 1) * kHeadVecs * sizeof(int4)), "alloc head records");
   BFS_CUDA(cudaMalloc(&g->deg, ((size_t)g->n_ni + 4) * 4), "alloc degrees");
-  dev_bytes += ((int64_t)g->n_ni + 1) * 32 + ((int64_t)g->n_ni + 4) * 4;
+  dev_bytes += ((int64_t)g->n_ni + 1) * kHeadVecs * 16 + ((int64_t)g->n_ni + 4) * 4;
   if (g->n_ni > 0) {
     k_degree_stats<<<grid_for(g->n_ni), kB, 0, s>>>(g->off, g->n_ni, g->d, sub.as<unsigned long long>() + 4);
     k_heads<<<grid_for(g->n_ni), kB, 0, s>>>(g->off, g->col, g->caller_of, g->n_ni, g->head, g->deg);
