@@ -736,6 +736,68 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
   }
 }
 
+// Level 0 forward, directly from the source's row: F_0 = {s}, so every row
+// entry u is new at depth 1 with parent s (the row holds no loop and no
+// duplicate).  All warps take 32-entry pieces of the row; each writes depth and
+// parent, sets u's bits in N and in the next visited bitmap (which the set-up
+// seeded with {s}), appends u to the next queue (normal) or its row chunks to
+// the next chunk list (delegate), and counts n_f and m_f.  This replaces the
+// expansion, its barrier and the bitmap sweep of a general forward level (with
+// atomicMin parents; the PULL option keeps the general level and its pass).
+__device__ void first_level(const BfsParams& p, int s, uint32_t* __restrict__ Vn, uint32_t* __restrict__ N,
+                            int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* sn, Acc& acc) {
+  const int lane = lane_id();
+  const int64_t gwarp = spread_warp();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t rb = p.off[s], re = p.off[s + 1];
+  for (int64_t e0 = rb + gwarp * 32; e0 < re; e0 += nwarps * 32) {
+    const int64_t e = e0 + lane;
+    const bool act = e < re;
+    const int u = act ? p.col[e] : 0;
+    const int dg = act ? p.deg[u] : 0;
+    if (act) {
+      p.depth_i[u] = 1;
+      p.parent_i[u] = p.src_c;
+      atomicOr(N + (u >> 5), 1u << (u & 31));
+      atomicOr(Vn + (u >> 5), 1u << (u & 31));
+      acc.nf += 1;
+      acc.mf += (unsigned long long)dg;
+    }
+    const unsigned nm = __ballot_sync(kFull, act && u >= p.d);
+    if (nm) {
+      unsigned long long qb = 0;
+      if (lane == 0) qb = atomicAdd(&sn->qn, (unsigned long long)__popc(nm));
+      qb = __shfl_sync(kFull, qb, 0);
+      if ((nm >> lane) & 1u) Q[qb + __popc(nm & ((1u << lane) - 1u))] = u;
+    }
+    const long long nc = (act && u < p.d) ? ((long long)dg + kChunk - 1) / kChunk : 0;
+    if (__any_sync(kFull, nc != 0)) {  // delegates: their row chunks, 32 entries per step
+      long long ci = nc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(kFull, ci, o);
+        if (lane >= o) ci += t;
+      }
+      const long long C = __shfl_sync(kFull, ci, 31);
+      unsigned long long cbase = 0;
+      if (lane == 0) cbase = atomicAdd(&sn->nch, (unsigned long long)C);
+      cbase = __shfl_sync(kFull, cbase, 0);
+      for (long long c0 = 0; c0 < C; c0 += 32) {
+        const long long c = c0 + lane;
+        int o = 0;
+#pragma unroll
+        for (int sh = 16; sh >= 1; sh >>= 1) {
+          const long long t = __shfl_sync(kFull, ci, o + sh - 1);
+          if (t <= c) o += sh;
+        }
+        const int ov = __shfl_sync(kFull, u, o);
+        const long long oex = __shfl_sync(kFull, ci, o) - __shfl_sync(kFull, nc, o);
+        if (c < C) CL[cbase + c] = make_int2(ov, (int)(c - oex));
+      }
+    }
+  }
+}
+
 // Canonical parents of the vertices found by a forward level, by a first-hit
 // scan of their sorted rows (the PULL option).
 __device__ void pull_parents(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, Acc& acc) {
@@ -855,6 +917,7 @@ __device__ void run_body(const BfsParams& p) {
       v4.w = t == 3 ? sbit : 0u;
     }
     reinterpret_cast<uint4*>(p.V)[q] = v4;
+    reinterpret_cast<uint4*>(p.V1)[q] = v4;  // level 0 adds the source's row to this copy
     reinterpret_cast<uint4*>(p.N0)[q] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(p.N1)[q] = make_uint4(0, 0, 0, 0);
   }
@@ -951,7 +1014,17 @@ __device__ void run_body(const BfsParams& p) {
       s_prev_nf = nf;
       return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni);
     };
-    if (dir == 0) {
+    if (dir == 0 && L == 0 && p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
+      first_level(p, src_i, Vn, Ncur, p.Q1, p.CL1, sn, acc);
+      if (trace) trace_done(sc);
+      if (leader) s_te = gtimer();
+      flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+      if (leader) {
+        p.slot[2] = LevelSlot();
+        p.slot[2].t_first = ~0ull;
+      }
+      bits = grid_sync(p, seq, master);
+    } else if (dir == 0) {
       expand_td(p, Vc, L);
       if (trace) trace_done(sc);
       if (grid_sync(p, seq, no_master) < 0) return;

@@ -310,3 +310,24 @@ def test_group_scan_hit_positions(th, shift):
     og = oracle.Graph(n, e[:, 0], e[:, 1])
     g = gpu_graph(n, e[:, 0], e[:, 1], th=th, schedule=2)
     check_against_oracle(og, g, sources, stats=True, th=th)
+
+
+@pytest.mark.parametrize("th", [16, 10**9])
+def test_first_level_from_source_row(th):
+    """Level 0 runs straight from the source's row: a centre with 3000 leaves (six
+    delegate chunks, or a normal row with TH 10^9) and a leaf whose only
+    neighbour is that centre, in every schedule and both parent options; a
+    few leaf-leaf edges give level 1 visited neighbours.  Depth, parent and the
+    per-level counters equal the oracle's."""
+    need_cuda()
+    n_leaf = 3000
+    e = [(0, x) for x in range(1, n_leaf + 1)] + [(x, x + 1) for x in range(1, 40, 2)]
+    e += [(n_leaf + 1, n_leaf + 2), (n_leaf + 2, 0)]
+    e = np.asarray(e, np.int32)
+    n = n_leaf + 5
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=th)
+    for sched, opts in SCHEDULES.items():
+        for tdp in (0, 1):
+            g.set_options(td_parent=tdp, **opts)
+            check_against_oracle(og, g, [0, 7, n_leaf, n_leaf + 1, n_leaf + 4], stats=True, th=th)
