@@ -170,6 +170,23 @@ typedef struct bfs_stats {
 int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* parent, bfs_stats* stats,
             struct CUstream_st* stream);
 
+/* Many BFS runs of one graph, results to host memory, pipelined: while the
+ * results of run i cross the host link (copy engine), run i+1 computes on the
+ * device.  Not in the paper, which reports device time only.
+ * sources[count]: caller ids.  depth[i], parent[i]: caller-owned HOST buffers
+ * of n int32 each, laid out as bfs_run's (page-locked buffers overlap the copy
+ * with the next run; pageable ones work but without the overlap).  A buffer may
+ * appear more than once: the later run's result lands last.
+ * status (optional, host [count]): each run's BFS_OK or error code.
+ * Ordering: the copies start after the work queued on `stream` before the call;
+ * the call returns after `stream` has synchronized, with every result in place.
+ * Device memory: two staging pairs (16·n bytes), a copy stream and events,
+ * made on first use and kept with the graph.  Same one-run-at-a-time rule as
+ * bfs_run.  Errors: INVALID (null, count < 0, source out of range, a device
+ * buffer), TIMEOUT (the first failing run's code), CUDA, OOM. */
+int bfs_run_many(bfs_graph* g, const int32_t* sources, int32_t count, int32_t* const* depth,
+                 int32_t* const* parent, int32_t* status, struct CUstream_st* stream);
+
 /* ---- Batched form: up to 64 queries per launch (64-lane bitset multi-source BFS). ----
  * Not in the paper, which runs one source at a time; the per-query result is the
  * same hop distance and canonical parent as bfs_run, with uint8 depth. */

@@ -129,6 +129,7 @@ def _load():
     lib.bfs_graph_get_info.argtypes = [c_vp, ctypes.POINTER(bfs_graph_info)]
     lib.bfs_graph_export.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp]
     lib.bfs_run.argtypes = [c_vp, c_i32, c_vp, c_vp, ctypes.POINTER(bfs_stats), c_vp]
+    lib.bfs_run_many.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]
     lib.bfs_wait.argtypes = [c_vp, c_vp]
     lib.bfs_run_static.argtypes = [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp]
     lib.bfs_free.argtypes = [c_vp]
@@ -266,6 +267,24 @@ def bfs_run(g, source: int, depth, parent, stats: bfs_stats | None = None, strea
     (numpy arrays / pinned tensors)."""
     _check(_load().bfs_run(g, int(source), _ptr(depth), _ptr(parent),
                            ctypes.byref(stats) if stats is not None else None, _stream(stream)))
+
+
+def bfs_run_many(g, sources, depth, parent, status=None, stream=None):
+    """Pipelined runs with host results: sources (ints), depth/parent: lists of
+    host int32 buffers (numpy arrays / pinned tensors) of n entries, one pair per
+    source; status: optional int32 numpy array of len(sources)."""
+    k = len(sources)
+    if len(depth) != k or len(parent) != k:
+        raise ValueError("one depth and one parent buffer per source")
+    src = (c_i32 * max(k, 1))(*[int(x) for x in sources])
+    dp = (c_vp * max(k, 1))(*[_ptr(x).value for x in depth])
+    pp = (c_vp * max(k, 1))(*[_ptr(x).value for x in parent])
+    st = None
+    if status is not None:
+        if not (isinstance(status, np.ndarray) and status.dtype == np.int32 and status.size >= k):
+            raise ValueError("status must be an int32 numpy array of len(sources)")
+        st = c_vp(status.ctypes.data)
+    _check(_load().bfs_run_many(g, src, int(k), dp, pp, st, _stream(stream)))
 
 
 def bfs_wait(g, stream=None):
@@ -414,6 +433,20 @@ class Graph:
         st = bfs_stats() if stats else None
         bfs_run(self._h, source, depth, parent, st, stream)
         return (depth, parent, st) if stats else (depth, parent)
+
+    def run_many(self, sources, depth=None, parent=None, stream=None):
+        """Pipelined runs with results in host memory (pinned tensors allocated when
+        not given).  Returns (depth list, parent list, status int32 array)."""
+        import torch
+
+        k = len(sources)
+        if depth is None:
+            depth = [torch.empty(self.n, dtype=torch.int32).pin_memory() for _ in range(k)]
+        if parent is None:
+            parent = [torch.empty(self.n, dtype=torch.int32).pin_memory() for _ in range(k)]
+        status = np.zeros(max(k, 1), dtype=np.int32)
+        bfs_run_many(self._h, sources, depth, parent, status, stream)
+        return depth, parent, status[:k]
 
     def wait(self, stream=None):
         bfs_wait(self._h, stream)

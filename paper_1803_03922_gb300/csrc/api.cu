@@ -1,5 +1,6 @@
 // C ABI of the library: options, graph life cycle, runs, statistics, errors.
 #include <cstring>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -103,6 +104,14 @@ void free_all(bfs_graph* g) {
                   g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (g->stage) cudaFree(g->stage);
+  for (int i = 0; i < 2; ++i) {
+    if (g->ev_run[i]) cudaEventDestroy(g->ev_run[i]);
+    if (g->ev_copy[i]) cudaEventDestroy(g->ev_copy[i]);
+  }
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->copy_stream) cudaStreamDestroy(g->copy_stream);
+  if (g->hdr_many) cudaFreeHost(g->hdr_many);
 }
 
 bool is_device_ptr(const void* p) {
@@ -341,6 +350,114 @@ extern "C" int bfs_run(bfs_graph* g, int32_t source, int32_t* depth, int32_t* pa
     if (rc) return rc;
     if (stats) return fill_stats(g, stats, h);
   }
+  return BFS_OK;
+}
+
+namespace {
+
+// Staging buffers, copy stream, events and header copies of bfs_run_many.
+int many_state(bfs_graph* g, int32_t count) {
+  const int64_t n4 = ((int64_t)g->n + 3) & ~(int64_t)3;
+  cudaError_t e = cudaSuccess;
+  if (!g->stage) {
+    e = cudaMalloc(&g->stage, (size_t)n4 * 4 * 4);
+    if (e != cudaSuccess) {
+      g->stage = nullptr;
+      return cuda_fail(e, "alloc staging buffers");
+    }
+    g->device_bytes += n4 * 16;
+  }
+  if (!g->copy_stream && (e = cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    g->copy_stream = nullptr;
+    return cuda_fail(e, "create copy stream");
+  }
+  for (int i = 0; i < 2; ++i) {
+    if (!g->ev_run[i] && (e = cudaEventCreateWithFlags(&g->ev_run[i], cudaEventDisableTiming)) != cudaSuccess) {
+      g->ev_run[i] = nullptr;
+      return cuda_fail(e, "create event");
+    }
+    if (!g->ev_copy[i] && (e = cudaEventCreateWithFlags(&g->ev_copy[i], cudaEventDisableTiming)) != cudaSuccess) {
+      g->ev_copy[i] = nullptr;
+      return cuda_fail(e, "create event");
+    }
+  }
+  if (!g->ev_join && (e = cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming)) != cudaSuccess) {
+    g->ev_join = nullptr;
+    return cuda_fail(e, "create event");
+  }
+  if (g->hdr_many_cap < count) {
+    if (g->hdr_many) cudaFreeHost(g->hdr_many);
+    g->hdr_many = nullptr;
+    g->hdr_many_cap = 0;
+    if ((e = cudaMallocHost((void**)&g->hdr_many, (size_t)count * sizeof(RunHeader))) != cudaSuccess) {
+      g->hdr_many = nullptr;
+      return cuda_fail(e, "alloc header copies");
+    }
+    g->hdr_many_cap = count;
+  }
+  return BFS_OK;
+}
+
+}  // namespace
+
+extern "C" int bfs_run_many(bfs_graph* g, const int32_t* sources, int32_t count, int32_t* const* depth,
+                            int32_t* const* parent, int32_t* status, struct CUstream_st* stream) {
+  if (!g) return fail(BFS_ERR_INVALID, "graph is NULL");
+  if (count < 0) return fail(BFS_ERR_INVALID, "count must be >= 0");
+  if (count == 0) return BFS_OK;
+  if (!sources || !depth || !parent) return fail(BFS_ERR_INVALID, "sources, depth or parent is NULL");
+  for (int32_t i = 0; i < count; ++i) {
+    if (sources[i] < 0 || sources[i] >= g->n) return fail(BFS_ERR_INVALID, "source out of range");
+    if (!depth[i] || !parent[i]) return fail(BFS_ERR_INVALID, "a depth or parent buffer is NULL");
+  }
+  DeviceGuard dg(g->device);
+  for (int32_t i = 0; i < count; ++i)
+    if (is_device_ptr(depth[i]) || is_device_ptr(parent[i]))
+      return fail(BFS_ERR_INVALID, "bfs_run_many writes host buffers (use bfs_run for device buffers)");
+  int rc = many_state(g, count);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream, x = g->copy_stream;
+  const int64_t n4 = ((int64_t)g->n + 3) & ~(int64_t)3;
+  const size_t bytes = (size_t)g->n * 4;
+  std::vector<unsigned> epoch((size_t)count, 0u);
+  // the copies start after the work already queued on `stream`
+  cudaError_t e = cudaEventRecord(g->ev_join, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(x, g->ev_join, 0);
+  int32_t launched = 0;
+  for (int32_t i = 0; i < count && e == cudaSuccess && rc == BFS_OK; ++i) {
+    const int slot = i & 1;
+    int32_t* sd = g->stage + (int64_t)slot * 2 * n4;
+    int32_t* sp = sd + n4;
+    if (i >= 2) e = cudaStreamWaitEvent(s, g->ev_copy[slot], 0);  // run i-2's copy has left the slot
+    if (e != cudaSuccess) break;
+    rc = launch_run(g, sources[i], sd, sp, s);
+    if (rc) break;
+    launched = i + 1;
+    epoch[(size_t)i] = g->epoch & 0x0FFFFFFFu;
+    e = cudaMemcpyAsync(g->hdr_many + i, g->hdr, sizeof(RunHeader), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_run[slot], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(x, g->ev_run[slot], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(depth[i], sd, bytes, cudaMemcpyDeviceToHost, x);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(parent[i], sp, bytes, cudaMemcpyDeviceToHost, x);
+    if (e == cudaSuccess) e = cudaEventRecord(g->ev_copy[slot], x);
+  }
+  // `stream` ends after the last copy; then every run's header is in place
+  cudaError_t e2 = cudaEventRecord(g->ev_join, x);
+  if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, g->ev_join, 0);
+  const cudaError_t e3 = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "bfs_run_many");
+  int first = BFS_OK;
+  for (int32_t i = 0; i < launched; ++i) {
+    const RunHeader& h = g->hdr_many[i];
+    int st = BFS_OK;
+    if (h.err != 0 && (h.err >> 4) == epoch[(size_t)i]) st = -(int)(h.err & 0xFu);
+    if (status) status[i] = st;
+    if (st != BFS_OK && first == BFS_OK) first = st;
+  }
+  if (first == BFS_ERR_TIMEOUT) return fail(first, "a device-side grid barrier wait passed its deadline");
+  if (first != BFS_OK) return fail(first, "the level-loop kernel reported an error");
   return BFS_OK;
 }
 

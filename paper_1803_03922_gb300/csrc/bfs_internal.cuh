@@ -139,6 +139,13 @@ struct bfs_graph {
   bfsgb::RunHeader* hdr = nullptr;
   unsigned long long* arrive = nullptr;  // [kMaxBlocks * 4]
   int32_t* out_scratch = nullptr;  // [2n], for runs with host output buffers
+  // bfs_run_many: two staging pairs of results and the stream and events that
+  // overlap one run's copy to the host with the next run (made on first use)
+  int32_t* stage = nullptr;        // [4 n4]: depth/parent of slot 0, then of slot 1
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_run[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr}, ev_join = nullptr;
+  bfsgb::RunHeader* hdr_many = nullptr;  // pinned host copies of the run headers
+  int64_t hdr_many_cap = 0;
   int grid_blocks = 0;
   int variant = 2;                 // CTAs per SM of the level-loop build in use
   unsigned int epoch = 0;          // runs launched

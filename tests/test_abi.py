@@ -48,6 +48,7 @@ def test_options_default_and_errors_without_gpu():
     assert lib.bfs_build_graph(None, None, 0, 0, None, ctypes.byref(h), None) == bfs.BFS_ERR_INVALID
     assert "num_vertices" in bfs.bfs_last_error()
     assert lib.bfs_run(None, 0, None, None, None, None) == bfs.BFS_ERR_INVALID
+    assert lib.bfs_run_many(None, None, 0, None, None, None, None) == bfs.BFS_ERR_INVALID
     lib.bfs_free(None)
 
 
