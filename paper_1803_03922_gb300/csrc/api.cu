@@ -152,23 +152,28 @@ void* pinned_device_ptr(void* p) {
 // Algorithmic HBM bytes of one run, from the per-level counters: forward level
 // 20*|F| + 8*m_f + 12*found (+ 16*found + 8*parent_edges with PULL parents);
 // backward level words*4 + 8*scanned +
-// 8*edges + 12*found; every level end 4 bitmap passes; a conversion one bitmap
-// pass + 4 per queue entry; the run's set-up 3 bitmap clears (+ 4*n_ni for
-// atomicMin parents) and the result pass 12*n + 8*reached + words*4.
+// 8*edges + 12*found; every level end 4 bitmap passes, except a level 0 run
+// straight from the source's row (forward, atomicMin parents); a conversion one
+// bitmap pass + 4 per queue entry, or only the 4 per entry when the sparse
+// backward level before built the queue; the run's set-up 4 bitmap clears
+// (+ 4*n_ni for atomicMin parents) and the result pass 12*n + 8*reached + words*4.
 int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st) {
   const int64_t bm = g->words * 4;  // one pass over a bitmap
-  int64_t b = 3 * bm + 12 * (int64_t)g->n + 8 * st->reached + bm;
-  if (g->opt.td_parent == BFS_TD_PARENT_ATOMICMIN) b += 4 * (int64_t)g->n_ni;
+  const bool atomicmin = g->opt.td_parent == BFS_TD_PARENT_ATOMICMIN;
+  int64_t b = 4 * bm + 12 * (int64_t)g->n + 8 * st->reached + bm;
+  if (atomicmin) b += 4 * (int64_t)g->n_ni;
   for (int L = 0; L < st->logged_levels; ++L) {
     const bfs_level_log& l = st->level[L];
     if (l.converted) b += bm + 4 * l.queue_entries;
+    // a sparse backward level that built this forward level's queue wrote its entries
+    else if (l.direction == 0 && L > 0 && st->level[L - 1].direction == 1) b += 4 * l.queue_entries;
     if (l.direction == 0) {
       b += 20 * l.frontier + 8 * l.frontier_edges + 12 * l.found;
       if (g->opt.td_parent == BFS_TD_PARENT_PULL) b += 16 * l.found + 8 * l.parent_edges;
     } else {
       b += bm + 8 * l.scanned + 8 * l.edges_examined + 12 * l.found;
     }
-    b += 4 * bm;
+    if (!(L == 0 && l.direction == 0 && atomicmin)) b += 4 * bm;
   }
   return b;
 }

@@ -21,6 +21,7 @@ static_assert(kHead == 2 || kHead == 4 || kHead == 8, "head records hold 2, 4 or
 constexpr int64_t kShort = 4096;      // rows with more entries left after the head go to the long-row path
 constexpr int kTailLanes = 4;         // lanes per row in the short-row group scan of a pull (2, 4, 8 or 16)
 constexpr int kTailPerLane = 4;       // row entries per lane and step there (1, or 2 / 4 as one 64- / 128-bit load)
+constexpr long long kListsFraction = 4;  // backward levels with under n_ni/4 unvisited build the next queue
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kMaxBlocks = 2048;      // upper bound of the level-loop grid (arrival words)
 

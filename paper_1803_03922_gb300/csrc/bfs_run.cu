@@ -472,6 +472,50 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
   return pos;
 }
 
+// Appends the vertices of this lane's word bits f (vertices v0 .. v0+31) to the
+// next forward level's lists: normal vertices to the queue Q, delegates as their
+// kChunk-entry row chunks to CL, with one reservation per list and warp
+// (warp-collective).  Backward levels with few unvisited vertices left call it,
+// so that a switch back to forward finds its frontier lists ready.
+__device__ void append_next(const BfsParams& p, int64_t v0, unsigned f, int32_t* __restrict__ Q,
+                            int2* __restrict__ CL, LevelSlot* slot) {
+  const int lane = lane_id();
+  unsigned dmask = 0;  // delegate bits of this lane's word
+  if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
+  const unsigned fn = f & ~dmask, fd = f & dmask;
+  if (__any_sync(kFull, fn != 0)) {
+    const int c = __popc(fn);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&slot->qn, (unsigned long long)incl);
+    base = __shfl_sync(kFull, base, 31) + (unsigned long long)(incl - c);
+    for (unsigned m = fn; m; m &= m - 1) Q[base++] = (int32_t)(v0 + __ffs(m) - 1);
+  }
+  if (__any_sync(kFull, fd != 0)) {
+    long long c = 0;
+    for (unsigned m = fd; m; m &= m - 1) c += ((long long)p.deg[v0 + __ffs(m) - 1] + kChunk - 1) / kChunk;
+    long long incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&slot->nch, (unsigned long long)incl);
+    base = __shfl_sync(kFull, base, 31) + (unsigned long long)(incl - c);
+    for (unsigned m = fd; m; m &= m - 1) {
+      const int v = (int)(v0 + __ffs(m) - 1);
+      const int nc = (int)(((long long)p.deg[v] + kChunk - 1) / kChunk);
+      for (int k = 0; k < nc; ++k) CL[base++] = make_int2(v, k);
+    }
+  }
+}
+
 // One backward item: bitmap words [w0, w0+iw) (iw <= 32) of this warp.  Its
 // unvisited vertices are gathered 32 at a time (lane i takes the i-th one), so a
 // sparse item costs one batch, not one pass per word; two batches are in flight
@@ -480,7 +524,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int r) {
 // and each word is written to N once.
 __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
                         uint32_t* __restrict__ Nclr, int L, int64_t w0, int iw, unsigned* found,
-                        uint32_t* __restrict__ N, LevelSlot* sc, Acc& acc) {
+                        uint32_t* __restrict__ N, LevelSlot* sc, Acc& acc, LevelSlot* qslot) {
   bool deferred = false;
   const int lane = lane_id();
   const int64_t W = p.words;
@@ -555,13 +599,15 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
   // the warp owns its words: found bits, the next visited bitmap, and the other
   // discovered bitmap cleared for the level after (deferred rows add their bits
   // after the next grid barrier)
+  unsigned f = 0u;
   if (lane < iw && w < W) {
-    const unsigned f = found[lane];
+    f = found[lane];
     N[w] = f;
     Vn[w] = vraw | f;
     Nclr[w] = 0u;
     found[lane] = 0u;
   }
+  if (qslot) append_next(p, w * 32, f, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, qslot);
   __syncwarp();
   return deferred;
 }
@@ -572,7 +618,7 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
 // drain with dynamic hand-out, one row per warp and 128-bit loads, so that long
 // scans spread over the grid instead of stalling the warp that met them.
 __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
-                          uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc) {
+                          uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc, bool build_next) {
   __shared__ unsigned s_found[kMaxWarpsPerBlock][32];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
@@ -585,8 +631,9 @@ __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, u
   LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t nitems = (W + iw - 1) / iw;
   bool deferred = false;
+  LevelSlot* qslot = build_next ? p.slot + ((L + 1) & (kSlots - 1)) : nullptr;
   for (int64_t it = gwarp; it < nitems; it += nwarps)
-    deferred |= bu_item(p, Vc, Vn, Nclr, L, it * iw, iw, found, N, sc, acc);
+    deferred |= bu_item(p, Vc, Vn, Nclr, L, it * iw, iw, found, N, sc, acc, qslot);
   return deferred;
 }
 
@@ -595,7 +642,7 @@ __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, u
 // a shared counter in runs and scan them with 128-bit loads; a vertex found here
 // sets its bit in N with an atomic.
 __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn, int L,
-                                Acc& acc) {
+                                Acc& acc, bool build_next) {
   LevelSlot* sc = p.slot + (L & (kSlots - 1));
   uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
   const long long nl = (long long)__ldcg(&sc->nlong);
@@ -618,6 +665,16 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
         atomicOr(Vn + (v >> 5), 1u << (v & 31));
         acc.nf += 1;
         acc.mf += (unsigned long long)(re - rb);
+        if (build_next) {  // the next forward level's lists (see append_next)
+          LevelSlot* sq = p.slot + ((L + 1) & (kSlots - 1));
+          if (v >= p.d) {
+            ((L & 1) ? p.Q0 : p.Q1)[atomicAdd(&sq->qn, 1ull)] = v;
+          } else {
+            const long long nc = ((long long)(re - rb) + kChunk - 1) / kChunk;
+            const unsigned long long b = atomicAdd(&sq->nch, (unsigned long long)nc);
+            for (long long k = 0; k < nc; ++k) ((L & 1) ? p.CL0 : p.CL1)[b + k] = make_int2(v, (int)k);
+          }
+        }
       }
     }
   }
@@ -884,6 +941,8 @@ __global__ void __launch_bounds__(kThr, kMinBlocks) bfs_level_loop(BfsParams p) 
 
 // Bits a barrier's master hands to every CTA.
 constexpr int kBitBackward = 1, kBitDone = 2, kBitConvert = 4, kBitDrain = 8;
+// a backward level that also builds the next forward level's lists (bits 4-5: item width)
+constexpr int kBitLists = 64;
 __device__ __forceinline__ int iw_code(long long unvisited, int n_ni) {
   int c = 0;  // item width 4 << c words: about 64 unvisited vertices per backward item
   while (c < 3 && (long long)(4 << c) * unvisited < 2LL * n_ni) ++c;
@@ -974,13 +1033,15 @@ __device__ void run_body(const BfsParams& p) {
   if (leader) p.hdr->t_init = t_start;
   int L = 0;
   int vpar = 0;  // visited bitmap of the current level: V (0) or V1 (1)
+  bool lists_ready = false;  // the previous (backward) level built this level's forward lists
   while (!(bits & kBitDone)) {
     // Bounds against a run that does not end: at most n_ni+1 levels, and the
     // run's deadline.  A failure set here ends every CTA at its next barrier.
     if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
       set_failed(p, BFS_ERR_TIMEOUT);
     const int dir = (bits & kBitBackward) ? 1 : 0;
-    const bool conv = (bits & kBitConvert) != 0;
+    const bool conv = (bits & kBitConvert) != 0 && !lists_ready;
+    const bool build_lists = dir == 1 && (bits & kBitLists) != 0;
     const int iw = 4 << ((bits >> 4) & 3);
     LevelSlot* sc = p.slot + (L & (kSlots - 1));
     LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
@@ -1012,7 +1073,10 @@ __device__ void run_body(const BfsParams& p) {
       if (nf == 0) return kBitDone;
       const int nd = decide(p, L + 1, dir, nf, mf, s_prev_nf, s_mu, s_unv);
       s_prev_nf = nf;
-      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni);
+      // a backward level with few unvisited vertices left builds the next
+      // forward level's lists as it goes, so a switch back needs no conversion
+      const int lists = (nd && s_unv * kListsFraction < (long long)p.n_ni) ? kBitLists : 0;
+      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni) | lists;
     };
     if (dir == 0 && L == 0 && p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
       first_level(p, src_i, Vn, Ncur, p.Q1, p.CL1, sn, acc);
@@ -1046,7 +1110,7 @@ __device__ void run_body(const BfsParams& p) {
     } else {
       // backward: the items write N, Vn and the cleared other bitmap themselves,
       // so one barrier ends the level unless long rows were deferred
-      const bool deferred = expand_bu(p, Vc, Vn, Noth, L, iw, acc);
+      const bool deferred = expand_bu(p, Vc, Vn, Noth, L, iw, acc, build_lists);
       flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
       if (trace) trace_done(sc);
       if (leader) {
@@ -1057,7 +1121,7 @@ __device__ void run_body(const BfsParams& p) {
       bits = grid_sync(p, seq, [&](int fl) { return (fl & kBitDrain) ? kBitDrain : master(fl); },
                        deferred ? kBitDrain : 0);
       if (bits >= 0 && (bits & kBitDrain)) {
-        drain_long_rows(p, Vc, Vn, L, acc);
+        drain_long_rows(p, Vc, Vn, L, acc, build_lists);
         flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
         bits = grid_sync(p, seq, master);
       }
@@ -1080,6 +1144,7 @@ __device__ void run_body(const BfsParams& p) {
       lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
       lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
     }
+    lists_ready = build_lists;
     vpar ^= 1;
     ++L;
   }
