@@ -153,7 +153,8 @@ void* pinned_device_ptr(void* p) {
 // 20*|F| + 8*m_f + 12*found (+ 16*found + 8*parent_edges with PULL parents);
 // backward level words*4 + 8*scanned +
 // 8*edges + 12*found; every level end 4 bitmap passes, except a level 0 run
-// straight from the source's row (forward, atomicMin parents); a conversion one
+// straight from the source's row (forward, atomicMin parents) and a forward
+// level that found nothing; a conversion one
 // bitmap pass + 4 per queue entry, or only the 4 per entry when the sparse
 // backward level before built the queue; the run's set-up 4 bitmap clears
 // (+ 4*n_ni for atomicMin parents) and the result pass 12*n + 8*reached + words*4.
@@ -173,7 +174,9 @@ int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st) {
     } else {
       b += bm + 8 * l.scanned + 8 * l.edges_examined + 12 * l.found;
     }
-    if (!(L == 0 && l.direction == 0 && atomicmin)) b += 4 * bm;
+    // no level-end sweeps after level 0 from the source's row, nor after a
+    // forward level that found nothing (the run ends at its first barrier)
+    if (!(L == 0 && l.direction == 0 && atomicmin) && !(l.direction == 0 && l.found == 0)) b += 4 * bm;
   }
   return b;
 }

@@ -326,10 +326,11 @@ __device__ int pull_head(const BfsParams& p, bool act, int v, const uint32_t* __
 // frontier vertex's caller id is also offered to v's parent slot.  Which lane
 // set the bit does not matter: the level end builds the next frontier from N.
 __device__ __forceinline__ void td_edge(const BfsParams& p, const uint32_t* __restrict__ Vc, int v, int pcaller,
-                                        uint32_t* __restrict__ N) {
+                                        uint32_t* __restrict__ N, bool& found) {
   if (v < 0) return;
   const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
   if (Vc[w] & bit) return;
+  found = true;
   if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
   if (!(p.tuning & 1) || !(__ldcg(N + w) & bit)) atomicOr(N + w, bit);
 }
@@ -337,13 +338,14 @@ __device__ __forceinline__ void td_edge(const BfsParams& p, const uint32_t* __re
 // Four row entries of one lane: the four visited-bit probes are issued before
 // any reduction, so they are in flight together.
 __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __restrict__ Vc, const int (&v)[4],
-                                         int pcaller, uint32_t* __restrict__ N) {
+                                         int pcaller, uint32_t* __restrict__ N, bool& found) {
   unsigned vw[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? Vc[(unsigned)v[t] >> 5] : kFull;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
+    found = true;
     if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], pcaller);
     uint32_t* nw = N + ((unsigned)v[t] >> 5);
     const unsigned bit = 1u << (v[t] & 31);
@@ -355,7 +357,7 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
 // concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
 // whose inclusive degree prefix first exceeds e).
 __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, const int32_t* __restrict__ Qc,
-                         int64_t qn, int64_t b, uint32_t* __restrict__ N) {
+                         int64_t qn, int64_t b, uint32_t* __restrict__ N, bool& found) {
   const int lane = lane_id();
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
@@ -380,12 +382,13 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
     const int64_t ob = __shfl_sync(kFull, beg, pos);
     const int64_t ox = __shfl_sync(kFull, excl, pos);
     const int opc = __shfl_sync(kFull, pc, pos);
-    td_edge(p, Vc, e < total ? p.col[ob + (e - ox)] : -1, opc, N);
+    td_edge(p, Vc, e < total ? p.col[ob + (e - ox)] : -1, opc, N, found);
   }
 }
 
 // One kChunk-entry piece of a delegate's row, 128-bit loads.
-__device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, int2 ck, uint32_t* __restrict__ N) {
+__device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, int2 ck, uint32_t* __restrict__ N,
+                         bool& found) {
   const int lane = lane_id();
   const int u = ck.x;
   const int64_t rb = p.off[u], re = p.off[u + 1];
@@ -401,11 +404,11 @@ __device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, in
     if (ja < end) {
       const int v[4] = {ja >= beg ? ca.x : -1, (ja + 1 >= beg && ja + 1 < end) ? ca.y : -1,
                         (ja + 2 >= beg && ja + 2 < end) ? ca.z : -1, (ja + 3 >= beg && ja + 3 < end) ? ca.w : -1};
-      td_edge4(p, Vc, v, pc, N);
+      td_edge4(p, Vc, v, pc, N, found);
     }
     if (jb < end) {
       const int v[4] = {cb.x, jb + 1 < end ? cb.y : -1, jb + 2 < end ? cb.z : -1, jb + 3 < end ? cb.w : -1};
-      td_edge4(p, Vc, v, pc, N);
+      td_edge4(p, Vc, v, pc, N, found);
     }
   }
 }
@@ -437,7 +440,7 @@ struct WorkCursor {
 // Work items of a forward level: the delegate chunks of F_L, then the normal
 // queue in batches of 32; warp w takes items w, w + warps, ... (a shared counter
 // measured slower here: the chunks are uniform).
-__device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, int L) {
+__device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, bool& found) {
   const LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sc->qn);
   const int64_t nch = (int64_t)__ldcg(&sc->nch);
@@ -449,9 +452,9 @@ __device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, i
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = gwarp; it < total; it += nwarps) {
     if (it < nch)
-      td_chunk(p, Vc, CLc[it], N);
+      td_chunk(p, Vc, CLc[it], N, found);
     else
-      td_batch(p, Vc, Qc, qn, it - nch, N);
+      td_batch(p, Vc, Qc, qn, it - nch, N, found);
   }
 }
 
@@ -943,6 +946,8 @@ __global__ void __launch_bounds__(kThr, kMinBlocks) bfs_level_loop(BfsParams p) 
 constexpr int kBitBackward = 1, kBitDone = 2, kBitConvert = 4, kBitDrain = 8;
 // a backward level that also builds the next forward level's lists (bits 4-5: item width)
 constexpr int kBitLists = 64;
+// arrival flag of a forward expansion's barrier: the CTA met an unvisited target
+constexpr int kFlagFound = 16;
 __device__ __forceinline__ int iw_code(long long unvisited, int n_ni) {
   int c = 0;  // item width 4 << c words: about 64 unvisited vertices per backward item
   while (c < 3 && (long long)(4 << c) * unvisited < 2LL * n_ni) ++c;
@@ -1034,6 +1039,7 @@ __device__ void run_body(const BfsParams& p) {
   int L = 0;
   int vpar = 0;  // visited bitmap of the current level: V (0) or V1 (1)
   bool lists_ready = false;  // the previous (backward) level built this level's forward lists
+  bool ended = false;        // a forward level found nothing and ended the run before its sweep
   while (!(bits & kBitDone)) {
     // Bounds against a run that does not end: at most n_ni+1 levels, and the
     // run's deadline.  A failure set here ends every CTA at its next barrier.
@@ -1089,24 +1095,34 @@ __device__ void run_body(const BfsParams& p) {
       }
       bits = grid_sync(p, seq, master);
     } else if (dir == 0) {
-      expand_td(p, Vc, L);
+      bool found = false;  // this thread met an unvisited target
+      expand_td(p, Vc, L, found);
       if (trace) trace_done(sc);
-      if (grid_sync(p, seq, no_master) < 0) return;
+      // a level that met no unvisited target found nothing: its barrier's master
+      // ends the run at once (no sweep, no second barrier; V stays depth <= L)
+      const int eb = grid_sync(p, seq, [&](int fl) { return (fl & kFlagFound) ? 0 : master(fl); },
+                               found ? kFlagFound : 0);
+      if (eb < 0) return;
       if (leader) s_te = gtimer();
-      // the next frontier's queues, depths and counts; Vn = Vc | N
-      frontier_from_bitmap(p, Vc, Vn, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true, true,
-                           L + 1, acc);
-      flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
-      if (p.td_parent == BFS_TD_PARENT_PULL) {
-        if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
-        pull_parents(p, Vc, L, acc);
-        flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+      if (eb & kBitDone) {
+        bits = eb;
+        ended = true;
+      } else {
+        // the next frontier's queues, depths and counts; Vn = Vc | N
+        frontier_from_bitmap(p, Vc, Vn, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true,
+                             true, L + 1, acc);
+        flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+        if (p.td_parent == BFS_TD_PARENT_PULL) {
+          if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
+          pull_parents(p, Vc, L, acc);
+          flush_block(acc, nullptr, nullptr, nullptr, nullptr, &sc->fix_edges);
+        }
+        if (leader) {
+          p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+          p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
+        }
+        bits = grid_sync(p, seq, master);
       }
-      if (leader) {
-        p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
-        p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
-      }
-      bits = grid_sync(p, seq, master);
     } else {
       // backward: the items write N, Vn and the cleared other bitmap themselves,
       // so one barrier ends the level unless long rows were deferred
@@ -1145,7 +1161,7 @@ __device__ void run_body(const BfsParams& p) {
       lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
     }
     lists_ready = build_lists;
-    vpar ^= 1;
+    if (!ended) vpar ^= 1;
     ++L;
   }
 
