@@ -948,9 +948,13 @@ constexpr int kBitBackward = 1, kBitDone = 2, kBitConvert = 4, kBitDrain = 8;
 constexpr int kBitLists = 64;
 // arrival flag of a forward expansion's barrier: the CTA met an unvisited target
 constexpr int kFlagFound = 16;
-__device__ __forceinline__ int iw_code(long long unvisited, int n_ni) {
-  int c = 0;  // item width 4 << c words: about 64 unvisited vertices per backward item
-  while (c < 3 && (long long)(4 << c) * unvisited < 2LL * n_ni) ++c;
+// Item width 4 << c words of a backward level: about 64 unvisited vertices per
+// item, or 128 when under 1/64 of the vertices are delegates (a graph of
+// near-uniform degree, whose rows cost alike, so wider items lose no balance).
+__device__ __forceinline__ int iw_code(long long unvisited, const BfsParams& p) {
+  const long long per = (long long)p.d * 64 < (long long)p.n_ni ? 4 : 2;
+  int c = 0;
+  while (c < 3 && (long long)(4 << c) * unvisited < per * p.n_ni) ++c;
   return c << 4;
 }
 
@@ -1030,7 +1034,7 @@ __device__ void run_body(const BfsParams& p) {
   if (p.test_skip_barrier && blockIdx.x == 0) return;  // the others' bounded wait must expire
   int bits = grid_sync(p, seq, [&](int) {
     return (src_in ? 0 : kBitDone) | (decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv) ? kBitBackward : 0) |
-           iw_code(s_unv, p.n_ni);
+           iw_code(s_unv, p);
   });
   if (bits < 0) return;
 
@@ -1082,7 +1086,7 @@ __device__ void run_body(const BfsParams& p) {
       // a backward level with few unvisited vertices left builds the next
       // forward level's lists as it goes, so a switch back needs no conversion
       const int lists = (nd && s_unv * kListsFraction < (long long)p.n_ni) ? kBitLists : 0;
-      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p.n_ni) | lists;
+      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p) | lists;
     };
     if (dir == 0 && L == 0 && p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
       first_level(p, src_i, Vn, Ncur, p.Q1, p.CL1, sn, acc);
