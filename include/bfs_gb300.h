@@ -128,7 +128,8 @@ int bfs_graph_export(const bfs_graph* g, int64_t* row_off, int32_t* col, int32_t
 /* One level of a run, as logged by the device. */
 typedef struct bfs_level_log {
   int32_t direction;      /* 0 forward (top-down), 1 backward (bottom-up) */
-  int32_t converted;      /* 1 if the frontier bitmap was converted to queues first */
+  int32_t converted;      /* 1 if the frontier bitmap was converted to queues first (0 when the
+                             sparse backward level before built the queues as it went) */
   int64_t frontier;       /* |F_L|: vertices at depth L */
   int64_t frontier_edges; /* m_f: sum of degrees over F_L */
   int64_t scanned;        /* backward: unvisited non-isolated vertices scanned */
