@@ -52,6 +52,20 @@ def test_options_default_and_errors_without_gpu():
     lib.bfs_free(None)
 
 
+def test_run_many_binding_checks_without_gpu():
+    import numpy as np
+
+    import paper_1803_03922_gb300 as bfs
+
+    host = np.zeros(8, np.int32)
+    with pytest.raises(ValueError):
+        bfs.bfs_run_many(None, [1, 2], [host], [host, host])  # one buffer pair per source
+    with pytest.raises(ValueError):
+        bfs.bfs_run_many(None, [1], [host], [host], status=np.zeros(1, np.int64))
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_run_many(None, [], [], [])  # the library rejects a NULL graph
+
+
 def test_product_path_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1803_03922_gb300")
     for dirpath, _, files in os.walk(pkg):
