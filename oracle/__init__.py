@@ -121,7 +121,8 @@ class Graph:
         return off, col[: self.nnz]
 
     def degree(self):
-        off, _ = self.csr()
+        off = np.empty(self.n + 1, dtype=np.int64)
+        self._lib.orc_graph_copy(self._h, _ptr(off), None)
         return np.diff(off)
 
     def bfs(self, s: int):

@@ -98,8 +98,8 @@ int32_t orc_graph_n(const orc_graph* g) { return g->n; }
 int64_t orc_graph_nnz(const orc_graph* g) { return g->nnz; }
 
 void orc_graph_copy(const orc_graph* g, int64_t* off, int32_t* col) {
-  memcpy(off, g->off, ((size_t)g->n + 1) * sizeof(int64_t));
-  if (g->nnz > 0) memcpy(col, g->col, (size_t)g->nnz * sizeof(int32_t));
+  if (off) memcpy(off, g->off, ((size_t)g->n + 1) * sizeof(int64_t));
+  if (col && g->nnz > 0) memcpy(col, g->col, (size_t)g->nnz * sizeof(int32_t));
 }
 
 /* Hop distance (Sec. VI-A.3: the output is the hop distance from the source),

@@ -47,7 +47,8 @@ orc_graph* orc_graph_build(int32_t n, int64_t m, const int32_t* src, const int32
 void orc_graph_free(orc_graph* g);
 int32_t orc_graph_n(const orc_graph* g);
 int64_t orc_graph_nnz(const orc_graph* g); /* directed entries = 2 x unique undirected edges */
-/* Copies the row offsets (n+1 entries) and the columns (nnz entries). */
+/* Copies the row offsets (n+1 entries) and the columns (nnz entries); a NULL
+ * destination skips that array. */
 void orc_graph_copy(const orc_graph* g, int64_t* off, int32_t* col);
 
 /* Hop distance by a FIFO-queue BFS, then the canonical parent by a separate pass:

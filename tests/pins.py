@@ -280,6 +280,12 @@ def pin_validator_detects(lib):
     d2 = d.copy(); d2[4] = -1; p2 = p.copy(); p2[4] = -1; checks.append((d2, p2, 2))
     d2 = d.copy(); d2[0] = 1; checks.append((d2, p, 1))
     p2 = p.copy(); p2[5] = 6; checks.append((d, p2, 7))
+    p2 = p.copy(); p2[1] = 3; checks.append((d, p2, 5))          # parent is a neighbour one level deeper
+    p2 = p.copy(); p2[3] = 4; checks.append((d, p2, 5))          # parent is a neighbour one level deeper
+    # Rule 8 (reached set = component of s) follows from rules 1-7: a parent chain
+    # falls one level per step, so it ends at the only vertex of depth 0, s, and
+    # no edge leaves the reached set.  A wrong union-find (a mutant) is caught by
+    # the oracle's own answer being rejected above.
     return all(g.validate(0, a, b) == want for a, b, want in checks)
 
 
@@ -403,6 +409,27 @@ def pin_level_counters_closed_forms(lib):
     return ok and c2[0][6] == 1 and list(c2[1][3:5]) == [0, 0]
 
 
+def pin_level_counters_first_hit(lib):
+    """Column 5 (forward parent pick: first-hit position + 1 in the sorted row)
+    and column 4 (backward k_v) where the first visited neighbour is not the
+    first entry.  Edges 0-4, 0-5, 5-6, 1-6, 2-6, 3-6 from source 0: depth 1 =
+    {4, 5}, depth 2 = {6}, depth 3 = {1, 2, 3}.  Row of 6 = [1, 2, 3, 5]: its
+    parent 5 is the fourth entry.  Forward everywhere: level 0 picks for 4 ([0])
+    and 5 ([0, 6]) one entry each = 2; level 1 picks for 6 = 4; level 2 picks
+    for 1, 2, 3 (rows [6]) = 3.  Level 1 backward: the unvisited non-isolated
+    vertices at its start are 1, 2, 3 (row [6], 6 unvisited: k = 1 each) and 6
+    (k = 4): scanned 4, sum of k = 7."""
+    g = _g(7, [(0, 4), (0, 5), (5, 6), (1, 6), (2, 6), (3, 6)], lib)
+    d, _ = g.bfs(0)
+    if d.tolist() != [0, 3, 3, 3, 1, 1, 2]:
+        return False
+    c = g.level_counters(0, d, 64, np.zeros(4, np.int32))
+    if [int(c[L][5]) for L in range(4)] != [2, 4, 3, 0]:
+        return False
+    c = g.level_counters(0, d, 64, np.array([0, 1, 0, 0], np.int32))
+    return list(c[1][3:5]) == [4, 7] and int(c[1][5]) == 0
+
+
 def pin_directions_worked(lib):
     """Both direction rules against the hand-worked levels of
     tests/golden/directions_worked.txt (Sec. IV-B)."""
@@ -460,8 +487,8 @@ PINS = [
     pin_even_cycle, pin_components_and_isolated, pin_dedup_selfloops, pin_exhaustive_5,
     pin_random_small_floyd, pin_scipy_depth_components, pin_invariants_python,
     pin_validator_detects, pin_component_edges, pin_builder_sets, pin_separation,
-    pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms, pin_directions_worked,
-    pin_directions_limits,
+    pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms, pin_level_counters_first_hit,
+    pin_directions_worked, pin_directions_limits,
 ]
 
 

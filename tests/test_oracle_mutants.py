@@ -37,6 +37,9 @@ MUTANTS = [
     ("u8_no_overflow", "if (dv > 254) overflow = 1;", ""),
     ("validator_no_canonical", "if (u < p && depth[u] == depth[v] - 1) return 6;", ""),
     ("validator_no_cut", "if ((depth[u] >= 0) != (depth[v] >= 0)) return 2;", ""),
+    ("validator_no_parent_depth", "if (depth[p] != depth[v] - 1) return 5;", ""),
+    ("validator_union_find_never_unites", "if (a != b) uf[a] = b;", ""),
+    ("first_hit_counts_from_zero", "o[5] += first_hit(g, depth, v, L);", "o[5] += first_hit(g, depth, v, L) - 1;"),
     ("subgraph_source_only", "counts[(u_del << 1) | v_del] += 1;", "counts[(u_del << 1) | u_del] += 1;"),
     ("paper_bv_swapped", "bv = sd * (qd + sd) / qd;", "bv = qd * (qd + sd) / sd;"),
     ("paper_back_flipped", "!(fvd < factor1 * bv)", "!(fvd > factor1 * bv)"),
