@@ -68,6 +68,9 @@ def _bind(lib):
     lib.orc_level_counters.argtypes = [P, i32, P, i64, i32, P, P]
     lib.orc_directions.restype = ctypes.c_int
     lib.orc_directions.argtypes = [P, i32, P, i32, i64, i64, ctypes.c_double, ctypes.c_double, i32, P]
+    if hasattr(lib, "orc_subgraph_directions"):
+        lib.orc_subgraph_directions.restype = ctypes.c_int
+        lib.orc_subgraph_directions.argtypes = [P, i32, P, i64, P, P, i32, P]
     return lib
 
 
@@ -189,6 +192,21 @@ class Graph:
                                       float(factor1), cap, _ptr(out))
         if rc < 0:
             raise ValueError("orc_directions failed with code %d" % rc)
+        return out[:rc].copy()
+
+    def subgraph_directions(self, s: int, depth, th: int, factor0=(0.5, 0.05, 1e-7), factor1=(1e-7, 1e-7, 1e-7)):
+        """Per-level directions of the dd, dn and nd visits (Sec. IV-B, each with its
+        own factor pair; nn always forward) on the run from s: int32 [levels],
+        bit 0 dd, bit 1 dn, bit 2 nd backward."""
+        depth = np.ascontiguousarray(depth, dtype=np.int32)
+        cap = int(depth.max()) + 2 if depth.size else 1
+        out = np.zeros(cap, dtype=np.int32)
+        f0 = np.ascontiguousarray(factor0, dtype=np.float64)
+        f1 = np.ascontiguousarray(factor1, dtype=np.float64)
+        rc = self._lib.orc_subgraph_directions(self._h, int(s), _ptr(depth), int(th), _ptr(f0), _ptr(f1), cap,
+                                               _ptr(out))
+        if rc < 0:
+            raise ValueError("orc_subgraph_directions failed with code %d" % rc)
         return out[:rc].copy()
 
     def subgraph_counts(self, th: int):

@@ -370,3 +370,66 @@ int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t 
   free(fv);
   return levels;
 }
+
+/* Sec. IV-B, per subgraph: the dd, dn and nd visits each take their own
+ * direction with their own factor pair; nn is always forward.  For a subgraph
+ * X with source class S and destination class T (delegate: degree > th):
+ *   out_X(u) = neighbours of class T of a vertex u of class S (u's X entries),
+ *   in_X(v)  = neighbours of class S of a vertex v of class T (v's entries in
+ *              the reversed subgraph; v is a "source" of the reversed one);
+ *   q  = vertices of F_L in S with out_X > 0 (the subgraph's input frontier,
+ *        zero-out-degree vertices filtered out),  FV = their out_X summed,
+ *   U  = unvisited vertices of T with in_X > 0 (sources of the reversed
+ *        subgraph: the source list / masks the backward visit starts from),
+ *   s  = unvisited vertices of S with out_X > 0,
+ *   BV = U (q + s) / q  (in double);
+ * forward turns backward when FV > factor0 BV, backward turns forward when
+ * FV < factor1 BV; a subgraph with q = 0 has nothing to visit this level and
+ * keeps its direction.  "Unvisited" at level L: not in F_0..F_L. */
+int orc_subgraph_directions(const orc_graph* g, int32_t s, const int32_t* depth, int64_t th,
+                            const double factor0[3], const double factor1[3], int32_t max_levels, int32_t* dirs) {
+  if (!g || !depth || !dirs || !factor0 || !factor1 || s < 0 || s >= g->n || max_levels < 0 || th < 0)
+    return ORC_ERR_INVALID;
+  if (g->off[s + 1] == g->off[s]) return 0; /* isolated source: no level runs */
+  const int32_t n = g->n;
+  int32_t levels = 0;
+  for (int32_t v = 0; v < n; ++v)
+    if (depth[v] + 1 > levels) levels = depth[v] + 1;
+  /* per vertex: delegate or not, and its delegate / normal neighbours */
+  int64_t* ndel = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  if (!ndel) return ORC_ERR_OOM;
+  for (int32_t v = 0; v < n; ++v)
+    for (int64_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      const int32_t u = g->col[i];
+      if (g->off[u + 1] - g->off[u] > th) ndel[v] += 1;
+    }
+  /* subgraphs in the order dd, dn, nd: source class, destination class (1 = delegate) */
+  const int src_del[3] = {1, 1, 0}, dst_del[3] = {1, 0, 1};
+  int cur[3] = {0, 0, 0};
+  for (int32_t L = 0; L < levels; ++L) {
+    for (int x = 0; x < 3; ++x) {
+      int64_t q = 0, fv = 0, U = 0, su = 0;
+      for (int32_t v = 0; v < n; ++v) {
+        const int64_t deg = g->off[v + 1] - g->off[v];
+        const int is_del = deg > th;
+        const int64_t nb_del = ndel[v], nb_norm = deg - ndel[v];
+        const int64_t out_x = is_del == src_del[x] ? (dst_del[x] ? nb_del : nb_norm) : 0;
+        const int64_t in_x = is_del == dst_del[x] ? (src_del[x] ? nb_del : nb_norm) : 0;
+        const int unvisited = depth[v] == -1 || depth[v] > L;
+        if (depth[v] == L && out_x > 0) {
+          q += 1;
+          fv += out_x;
+        }
+        if (unvisited && in_x > 0) U += 1;
+        if (unvisited && out_x > 0) su += 1;
+      }
+      if (q > 0) {
+        const double qd = (double)q, sd = (double)su, bv = (double)U * (qd + sd) / qd, fvd = (double)fv;
+        cur[x] = cur[x] == 0 ? (fvd > factor0[x] * bv) : !(fvd < factor1[x] * bv);
+      }
+    }
+    if (L < max_levels) dirs[L] = cur[0] | (cur[1] << 1) | (cur[2] << 2);
+  }
+  free(ndel);
+  return levels;
+}

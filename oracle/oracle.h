@@ -122,6 +122,15 @@ int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int6
 int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t rule, int64_t alpha, int64_t beta,
                    double factor0, double factor1, int32_t max_levels, int32_t* dirs);
 
+/* Per-subgraph visit directions (Sec. IV-B: dd, dn and nd each switch with their
+ * own factor pair, nn is always forward) on the run from s with final depth
+ * `depth` and delegates of degree > th.  factor0/factor1[x] for x = 0 dd, 1 dn,
+ * 2 nd.  dirs[L] = bit 0 dd, bit 1 dn, bit 2 nd backward at level L (the level
+ * that expands F_L), for L < levels, at most max_levels of them; returns levels
+ * (0 for an isolated source) or an error.  See oracle.c for the quantities. */
+int orc_subgraph_directions(const orc_graph* g, int32_t s, const int32_t* depth, int64_t th,
+                            const double factor0[3], const double factor1[3], int32_t max_levels, int32_t* dirs);
+
 #ifdef __cplusplus
 }
 #endif

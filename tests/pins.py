@@ -449,6 +449,55 @@ def pin_directions_worked(lib):
     return True
 
 
+def pin_subgraph_directions_worked(lib):
+    """The per-subgraph rule against the hand-worked levels of
+    tests/golden/subgraph_directions_worked.txt (Sec. IV-B)."""
+    from tests.golden_io import read_subgraph_directions
+
+    graphs, cases = read_subgraph_directions()
+    for gname, src, f0, f1, want in cases:
+        n, th, s, d = graphs[gname]
+        g = oracle.Graph(n, s, d, lib=lib)
+        dep, _ = g.bfs(src)
+        if list(g.subgraph_directions(src, dep, th, f0, f1)) != want:
+            return False
+    return True
+
+
+def pin_subgraph_directions_reduce(lib, seed=23):
+    """Limit cases of the per-subgraph rule on random graphs: factor0 = 0 turns
+    every subgraph backward at its first level with a frontier (FV > 0 = 0 BV);
+    factor0 = infinity keeps all forward; with th at least the maximum degree
+    there are no delegates, so dd, dn and nd never have a frontier and stay
+    forward; with th = 0 every non-isolated vertex is a delegate, so only dd
+    has work, and its decisions follow the single paper rule (Sec. IV-B) with
+    U = s = the unvisited non-isolated vertices."""
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        n = int(rng.integers(5, 60))
+        m = int(rng.integers(n, 4 * n))
+        src, dst = _random_graph(rng, n, m)
+        g = oracle.Graph(n, src, dst, lib=lib)
+        s = int(src[0])
+        d, _ = g.bfs(s)
+        inf = float("inf")
+        if g.subgraph_directions(s, d, 2, (inf,) * 3, (0.0,) * 3).any():
+            return False
+        big = int(g.degree().max())
+        if g.subgraph_directions(s, d, big, (0.0,) * 3, (0.0,) * 3).any():
+            return False
+        for f0 in (0.05, 0.5, 2.0):
+            dd = g.subgraph_directions(s, d, 0, (f0, 0.5, 0.5), (1e-7, 1e-7, 1e-7))
+            one = g.directions(s, d, "paper", factor0=f0, factor1=1e-7)
+            if list(dd & 1) != list(one) or (dd & 6).any():
+                return False
+        allb = g.subgraph_directions(s, d, 2, (0.0,) * 3, (0.0,) * 3)
+        # a subgraph turns backward for good at the first level where it has a frontier
+        if not np.all(np.diff(allb & 1) >= 0) or not np.all(np.diff((allb >> 1) & 1) >= 0):
+            return False
+    return True
+
+
 def pin_directions_limits(lib, seed=17):
     """Limit cases of the rules on random graphs: factor0 = 0 goes backward at
     level 0 and (factor1 = 0) never returns; factor0 = inf or alpha = 0 never
@@ -488,7 +537,8 @@ PINS = [
     pin_random_small_floyd, pin_scipy_depth_components, pin_invariants_python,
     pin_validator_detects, pin_component_edges, pin_builder_sets, pin_separation,
     pin_subgraph_counts, pin_batch_u8, pin_level_counters_closed_forms, pin_level_counters_first_hit,
-    pin_directions_worked, pin_directions_limits,
+    pin_directions_worked, pin_directions_limits, pin_subgraph_directions_worked,
+    pin_subgraph_directions_reduce,
 ]
 
 

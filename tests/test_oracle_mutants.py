@@ -46,6 +46,12 @@ MUTANTS = [
     ("beamer_no_shrink_test", "q[L] * beta < (int64_t)g->n && q[L] < q_prev", "q[L] * beta < (int64_t)g->n"),
     ("beamer_mu_all_edges", "m_u = m_total - seen_m;", "m_u = m_total;"),
     ("directions_seen_after", "    seen_v += q[L];\n    seen_m += fv[L];\n", ""),
+    ("subgraph_U_from_source_class", "if (unvisited && in_x > 0) U += 1;", "if (unvisited && out_x > 0) U += 1;"),
+    ("subgraph_q_unfiltered", "if (depth[v] == L && out_x > 0) {", "if (depth[v] == L && is_del == src_del[x]) {"),
+    ("subgraph_s_counts_visited", "if (unvisited && out_x > 0) su += 1;", "if (out_x > 0) su += 1;"),
+    ("subgraph_dn_nd_swapped", "const int src_del[3] = {1, 1, 0}, dst_del[3] = {1, 0, 1};",
+     "const int src_del[3] = {1, 0, 1}, dst_del[3] = {1, 1, 0};"),
+    ("subgraph_factor_of_dd_for_all", "(fvd > factor0[x] * bv)", "(fvd > factor0[0] * bv)"),
 ]
 
 
