@@ -2,20 +2,23 @@
 """Benchmark: single-source direction-optimized BFS over a degree-separated graph
 on one GB300, GTEPS as the harmonic mean over 64 seeded sources.
 
-Workload (default): RMAT scale 22 (4,194,304 vertices, edge factor 16, a,b,c,d =
+Workload (default): RMAT scale 26 (67,108,864 vertices, edge factor 16, a,b,c,d =
 .57,.19,.19,.05, ids permuted, self-loops and duplicates removed), degree
-threshold TH = 64, Beamer alpha = 15 / beta = 18, 64 seeded non-isolated sources.
-A step is one BFS from each of the 64 sources.  GTEPS per run = unique undirected
-edges of the traversed component / device time of the run (CUDA events on the
-launching stream); the reported value is their harmonic mean.  The graph build is
-set-up, not timed (Graph500 convention).  The L2 is flushed (256 MiB write)
-before every timed run.
+threshold TH = 64, Beamer alpha = 15 / beta = 18, 64 seeded non-isolated sources,
+one query at a time through the persistent level-loop kernel.  A step is one BFS
+from each of the 64 sources.  GTEPS per run = unique undirected edges of the
+traversed component / device time of the run (CUDA events on the launching
+stream); the reported value is their harmonic mean.  The graph build is set-up,
+not timed (Graph500 convention).  Inputs are larger than L2, and the L2 is also
+flushed (256 MiB write) before every timed run.
 
-Also reported on the same line: the TH sweep 32/64/128/256 at scale 22, RMAT
-scale 26 and an Erdos-Renyi graph of 2^26 vertices / average degree 32 (device
-numbers), the end-to-end form with host result buffers, the roofline of the
-level-loop kernel against the measured HBM bandwidth, the device clocks during
-the timed region, and the CPU oracle timed on the host as a reference.
+Also reported on the same line: the roofline of the level-loop kernel (the
+algorithmic bytes of every run, level by level from its counters, over its
+device time, against the measured HBM bandwidth), the end-to-end form with host
+result buffers, the device clocks during the timed region, the CPU oracle timed
+on the host as a reference, and extras: RMAT scale 22 with its TH sweep, the
+Erdos-Renyi graph of 2^26 vertices / average degree 32, the batched form and the
+serving loop.
 
 `--impl reference` times the CPU oracle alone on the same workload.
 Multi-GPU (torchrun): independent replicas, one graph per GPU, no data exchange.
@@ -88,6 +91,54 @@ def hmean(xs):
 def gmean(xs):
     xs = [x for x in xs if x > 0]
     return math.exp(sum(math.log(x) for x in xs) / len(xs)) if xs else 0.0
+
+
+# ---- algorithmic bytes ----------------------------------------------------------------------
+
+def level_list(st):
+    """The logged levels of a run as plain dicts (direction and counters)."""
+    out = []
+    for i in range(st.logged_levels):
+        lv = st.level[i]
+        out.append({"dir": int(lv.direction), "frontier": int(lv.frontier), "m_f": int(lv.frontier_edges),
+                    "scanned": int(lv.scanned), "k": int(lv.edges_examined), "found": int(lv.found),
+                    "queue": int(lv.queue_entries)})
+    return out
+
+
+def algorithmic_bytes(levels, n, n_ni, d):
+    """Bytes one BFS must move, level by level, whatever the kernel does beyond
+    them (Sec. IV-A forward visit, Sec. II-C / IV-B backward visit, Sec. VI-A.3
+    output).  Bitmaps span the n_ni non-isolated vertices.
+      forward level:  per frontier vertex its offset pair (8 B) and its row
+                      (4 B per entry), one 4-byte state probe per row entry, and
+                      per newly reached vertex depth, parent, its queue entry
+                      written now and read by the next level (16 B);
+      backward level: one pass over the visited bitmap (n_ni/8 B), per scanned
+                      vertex its offset pair (8 B), per examined entry its column
+                      and the frontier probe (8 B), depth, parent and the
+                      frontier bit of each vertex found (12 B);
+      level end:      the delegate and the whole bitmap, read and written
+                      (2 (d/8 + n_ni/8) B), and the next level's queue (4 B per
+                      entry) when that level is forward; none after a level that
+                      found nothing;
+      output:         depth and parent of all n vertices (8n B), once per run.
+    Returns (per-level bytes summed, by phase: forward_expand, forward_level_end,
+    backward_level)."""
+    bm = n_ni / 8.0
+    ph = {"forward_expand": 0.0, "forward_level_end": 0.0, "backward_level": 0.0}
+    for i, lv in enumerate(levels):
+        end = 0.0
+        if lv["found"] > 0:
+            end = 2.0 * (d / 8.0 + bm)
+            if i + 1 < len(levels) and levels[i + 1]["dir"] == 0:
+                end += 4.0 * levels[i + 1]["queue"]
+        if lv["dir"] == 0:
+            ph["forward_expand"] += 8.0 * lv["frontier"] + 8.0 * lv["m_f"]
+            ph["forward_level_end"] += 16.0 * lv["found"] + end
+        else:
+            ph["backward_level"] += bm + 8.0 * lv["scanned"] + 8.0 * lv["k"] + 12.0 * lv["found"] + end
+    return sum(ph.values()) + 8.0 * n, ph
 
 
 # ---- clocks during the timed region ---------------------------------------------------------
@@ -215,43 +266,47 @@ class DeviceWorkload:
         self.info = self.g.info
         self.depth = torch.empty(self.n, dtype=torch.int32, device="cuda")
         self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
-        # untimed pass: per-source traversal size, byte model and level log
-        self.ce, self.model, self.levels, self.dirs, self.phase = [], [], [], [], []
-        # per phase: [model bytes, device ns] summed over the sources (level log)
+        # untimed pass: per-source traversal size, byte counts and level log
+        self.ce, self.model, self.alg, self.levels, self.dirs, self.phase = [], [], [], [], [], []
+        # per phase: [algorithmic bytes, device ns] summed over the sources (level log)
         self.phases = {"forward_expand": [0, 0], "forward_level_end": [0, 0], "backward_level": [0, 0]}
-        bm = 4 * ((self.info.n_nonisolated + 31) // 32)  # one pass over a bitmap
+        self.setup_result_ns = 0
         for s in self.sources:
             _, _, st = self.g.run(int(s), self.depth, self.parent, stats=True)
             self.ce.append(st.component_edges)
             self.model.append(st.model_bytes)
+            lvls = level_list(st)
+            alg, by_phase = algorithmic_bytes(lvls, self.n, self.info.n_nonisolated, self.info.delegates)
+            self.alg.append(alg)
             self.levels.append(st.levels)
-            self.dirs.append("".join("B" if st.level[i].direction else "T" for i in range(st.logged_levels)))
+            self.dirs.append("".join("B" if lv["dir"] else "T" for lv in lvls))
             td = bu = 0
+            for k in by_phase:
+                self.phases[k][0] += by_phase[k]
             for i in range(st.logged_levels):
                 lv = st.level[i]
                 dt = lv.t_end_ns - lv.t_begin_ns
                 if lv.direction:
                     bu += dt
-                    ph = self.phases["backward_level"]
-                    ph[0] += 5 * bm + 8 * lv.scanned + 8 * lv.edges_examined + 12 * lv.found
-                    ph[1] += dt
+                    self.phases["backward_level"][1] += dt
                 else:
                     td += dt
-                    ph = self.phases["forward_expand"]
-                    ph[0] += 20 * lv.frontier + 8 * lv.frontier_edges
-                    ph[1] += lv.t_expand_ns - lv.t_begin_ns
-                    ph = self.phases["forward_level_end"]
-                    ph[0] += 4 * bm + 12 * lv.found
-                    ph[1] += lv.t_end_ns - lv.t_expand_ns
+                    self.phases["forward_expand"][1] += lv.t_expand_ns - lv.t_begin_ns
+                    self.phases["forward_level_end"][1] += lv.t_end_ns - lv.t_expand_ns
+            self.setup_result_ns += st.setup_ns + st.result_ns
             self.phase.append((td, bu, st.device_ns))
 
     def phase_roofline(self, peak):
-        """Model bytes / device time of each phase over all sources (device timer of
-        the level log; each phase's time ends at the grid barrier that closes it)."""
+        """Algorithmic bytes / device time of each phase over all sources (device
+        timer of the level log; each phase's time ends at the grid barrier that
+        closes it), and the set-up plus result pass's share of the device time."""
         out = {}
         for k, (b, ns) in self.phases.items():
             if ns > 0:
-                out[k] = {"model_gb": b / 1e9, "ms": ns / 1e6, "achieved_gbs": b / ns, "frac": b / ns / peak}
+                out[k] = {"algorithmic_gb": b / 1e9, "ms": ns / 1e6, "achieved_gbs": b / ns, "frac": b / ns / peak}
+        dev = sum(p[2] for p in self.phase)
+        if dev:
+            out["setup_and_result_share"] = self.setup_result_ns / dev
         return out
 
     def timed(self, steps, flush, stream):
@@ -389,9 +444,40 @@ def replica_value(run_s, wall_s, edges, device):
     return float(e[0]) / run_max / 1e9, run_max, wall_max
 
 
+class OracleInfo:
+    """nnz, delegates and non-isolated vertices of the oracle's graph, the same
+    description the device graph gives of itself."""
+
+    def __init__(self, og, th):
+        import numpy as np
+
+        deg = og.degree()
+        self.nnz = og.nnz
+        self.delegates = int(np.count_nonzero(deg > th))
+        self.n_nonisolated = int(np.count_nonzero(deg > 0))
+
+
+def oracle_runs(og, sources, threads):
+    """One oracle BFS per source, up to `threads` at a time (each run is the
+    single-threaded oracle; runs share the read-only graph).  Returns per-run
+    (seconds, GTEPS)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(s):
+        t0 = time.perf_counter()
+        d, _ = og.bfs(int(s))
+        dt = time.perf_counter() - t0
+        return dt, og.component_edges(d) / dt / 1e9
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        return list(ex.map(one, sources))
+
+
 def run_reference(args, w, ws, rank):
-    """CPU oracle arm: each step is one BFS of the oracle from one of the same
-    seeded sources (a bounded sample of the workload)."""
+    """CPU oracle arm: each step is one BFS of the oracle (single-threaded) from
+    one of the same seeded sources on the same graph.  So that the whole run
+    stays within minutes at scale 26, independent runs go on up to one host core
+    each, concurrently; a run's time is its own wall time."""
     if rank != 0:
         return
     import graphgen
@@ -403,29 +489,26 @@ def run_reference(args, w, ws, rank):
     sources = sources_for(w, mask, 0)
     og = oracle.Graph(n, src, dst)
     del src, dst
+    info = OracleInfo(og, w["th"])
     k = len(sources)
-    for i in range(args.warmup):
-        og.bfs(int(sources[i % k]))
-    ts, vals = [], []
-    for i in range(args.steps):
-        s = int(sources[(args.warmup + i) % k])
-        t0 = time.perf_counter()
-        d, _ = og.bfs(s)
-        dt = time.perf_counter() - t0
-        ts.append(dt)
-        vals.append(og.component_edges(d) / dt / 1e9)
-    v = hmean(vals)
+    threads = min(os.cpu_count() or 1, 16, max(1, args.steps))
+    oracle_runs(og, [sources[i % k] for i in range(args.warmup)], threads)
+    res = oracle_runs(og, [sources[(args.warmup + i) % k] for i in range(args.steps)], threads)
+    ts = [r[0] for r in res]
+    v = hmean([r[1] for r in res])
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded RMAT, Graph500 parameters)",
-        "config": config_of(args.workload, w),
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "GTEPS",
-                         "sample": "one of the 64 seeded sources per step on the same graph "
-                                   "(single-threaded C, -O2)", "host": host_cpu()},
+        "config": dict(config_of(args.workload, w, info), parallelism="replicas" if ws > 1 else "single GPU"),
+        "cpu_baseline": {"kind": "oracle", "cores": threads, "value": v, "unit": "GTEPS",
+                         "sample": "one of the 64 seeded sources per step on the same graph; each run is the "
+                                   "single-threaded C oracle (-O2), up to %d runs at a time on separate host "
+                                   "cores" % threads, "host": host_cpu()},
         "e2e": {"value": v, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    og.close()
     print(json.dumps(line), flush=True)
 
 
@@ -742,7 +825,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extras", action="store_true", help="skip the TH sweep and the scale-26 graphs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and serving measurements")
@@ -802,8 +885,10 @@ def main():
         run_max = run_s
     k = len(dw.sources)
     model_total = sum(dw.model[i % k] for i in range(len(times)))
-    achieved = model_total / run_s / 1e9
+    alg_total = sum(dw.alg[i % k] for i in range(len(times)))
+    achieved = alg_total / run_s / 1e9
     peak, peak_kind = measured_peak_hbm()
+    traffic = ncu_traffic(args.workload)
     e2e_val, e2e_single, e2e_ms_pipelined, e2e_ms_single = e2e_runs(dw, max(1, min(args.steps, 3)))
     td_ns = sum(p[0] for p in dw.phase)
     bu_ns = sum(p[1] for p in dw.phase)
@@ -819,9 +904,12 @@ def main():
         "gpu_launches": len(times),
         "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": ncu_traffic(args.workload),
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "bfs_level_loop", "peak_kind": peak_kind,
-                     "model_bytes_per_launch": model_total / len(times)},
+                     "algorithmic_bytes_per_launch": alg_total / len(times),
+                     "traffic_over_algorithmic": traffic / (alg_total / len(times)) if traffic else None,
+                     "kernel_model_bytes_per_launch": model_total / len(times),
+                     "launch_ms_mean": 1e3 * run_s / len(times)},
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * dw.n * k},
         "detail": {"wall_ms_per_step_with_flush": 1e3 * wall / args.steps,
@@ -850,14 +938,25 @@ def main():
         extras = {"degree_classes_%s" % args.workload: degree_table(degree_rows),
                   "th_rule": {"rule": "64 * 2^((scale - 30) / 2) (Sec. VI-B)",
                               "th_by_scale": {str(sc): th_for_scale(sc) for sc in (16, 22, 24, 26, 30, 32)}}}
-        for th in th_space_for_scale(w["scale"]):
-            if args.workload != "rmat22" or th == w["th"]:
+        w22 = WORKLOADS["rmat22"]
+        for th in [w22["th"]] + [t for t in th_space_for_scale(22) if t != w22["th"]]:
+            if args.workload == "rmat22" and th == w22["th"]:
                 continue
-            d2 = DeviceWorkload("rmat22", w, rank, th=th)
-            t2 = d2.timed(1, flush, stream)
-            extras["rmat22_th%d" % th] = {"gteps": hmean(d2.gteps(t2)), "delegates": d2.info.delegates,
-                                          "roofline_frac": sum(d2.model) / sum(t2) / 1e9 / peak}
-            d2.close()
+            try:
+                d2 = DeviceWorkload("rmat22", w22, rank, th=th)
+                d2.timed(1, flush, stream)
+                t2 = d2.timed(2, flush, stream)
+                key = "rmat22" if th == w22["th"] else "rmat22_th%d" % th
+                extras[key] = {"gteps": hmean(d2.gteps(t2)), "delegates": d2.info.delegates,
+                               "ms_per_bfs_median": 1e3 * statistics.median(t2),
+                               "roofline_frac": sum(d2.alg[i % len(d2.sources)] for i in range(len(t2)))
+                               / sum(t2) / 1e9 / peak}
+                if th == w22["th"]:
+                    extras[key]["phase_roofline"] = d2.phase_roofline(peak)
+                    extras[key]["directions_first_source"] = d2.dirs[0]
+                d2.close()
+            except Exception as e:  # report, do not hide
+                extras["rmat22_th%d" % th] = {"error": str(e)}
         try:  # config 1: RMAT scale 16, top-down only, 64 sources
             w16 = dict(WORKLOADS["rmat16"])
             d1 = DeviceWorkload("rmat16", w16, rank)
@@ -865,30 +964,32 @@ def main():
             d1.timed(1, flush, stream)
             t1 = d1.timed(2, flush, stream)
             extras["rmat16_topdown"] = {"gteps": hmean(d1.gteps(t1)),
-                                        "ms_per_bfs_median": 1e3 * statistics.median(t1)}
+                                        "ms_per_bfs_median": 1e3 * statistics.median(t1),
+                                        "roofline_frac": sum(d1.alg[i % len(d1.sources)] for i in range(len(t1)))
+                                        / sum(t1) / 1e9 / peak,
+                                        "phase_roofline": d1.phase_roofline(peak)}
             d1.close()
         except Exception as e:  # report, do not hide
             extras["rmat16_topdown"] = {"error": str(e)}
-        if args.workload == "rmat22":
-            try:
-                extras["autotuned_rmat22"] = autotuned(w, rank, flush, stream, peak)
-            except Exception as e:  # report, do not hide
-                extras["autotuned_rmat22"] = {"error": str(e)}
+        try:
+            extras["autotuned_rmat22"] = autotuned(w22, rank, flush, stream, peak)
+        except Exception as e:  # report, do not hide
+            extras["autotuned_rmat22"] = {"error": str(e)}
         for key, name, th26 in (("rmat26", "rmat26", None), ("er26", "er26", None),
                                 ("rmat26_th%d" % th_for_scale(26), "rmat26", th_for_scale(26))):
+            if key == args.workload:
+                continue
             try:
                 d3 = DeviceWorkload(name, WORKLOADS[name], rank, th=th26)
                 d3.timed(1, None, stream)
                 t3 = d3.timed(2, None, stream)
                 extras[key] = {"gteps": hmean(d3.gteps(t3)), "ms_per_bfs_median": 1e3 * statistics.median(t3),
-                                "roofline_frac": sum(d3.model[i % len(d3.sources)] for i in range(len(t3)))
+                                "roofline_frac": sum(d3.alg[i % len(d3.sources)] for i in range(len(t3)))
                                 / sum(t3) / 1e9 / peak,
                                 "nnz": d3.info.nnz, "delegates": d3.info.delegates,
                                 "levels": statistics.median(d3.levels), "build_s": d3.build_s,
                                 "directions_first_source": d3.dirs[0],
                                 "phase_roofline": d3.phase_roofline(peak)}
-                if key == "rmat26":
-                    extras["degree_classes_rmat26"] = degree_table(d3.g.degree_classes(DEGREE_THS))
                 d3.close()
                 del d3
                 torch.cuda.empty_cache()
