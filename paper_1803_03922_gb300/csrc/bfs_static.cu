@@ -32,6 +32,8 @@ struct StaticHeader {
   unsigned long long n_f[2], m_f[2];  // next-frontier counters, by level parity
   unsigned long long pad[10];
 };
+// rows longer than this are walked by the whole warp (forward) or scanned by it (backward)
+constexpr int64_t kStaticWarpRow = 32;
 static_assert(sizeof(StaticHeader) <= 256, "header fits its slot");
 
 // Scratch shared by every call on this device: a 256-byte header, then the
@@ -103,6 +105,14 @@ __device__ bool st_sync(const StaticParams& p, StaticHeader* h) {
   return s_ok != 0;
 }
 
+// One forward row entry u->v: an unvisited target offers u as its parent
+// (atomicMin keeps the smallest) and sets its bit in N.
+__device__ __forceinline__ void st_push(const StaticParams& p, const uint32_t* V, uint32_t* N, int u, int v) {
+  if ((V[v >> 5] >> (v & 31)) & 1u) return;
+  atomicMin(p.parent + v, u);
+  atomicOr(N + (v >> 5), 1u << (v & 31));
+}
+
 __device__ void st_body(const StaticParams& p) {
   StaticHeader* h = reinterpret_cast<StaticHeader*>(p.scratch);
   uint32_t* V = reinterpret_cast<uint32_t*>(p.scratch + 256);
@@ -129,6 +139,24 @@ __device__ void st_body(const StaticParams& p) {
     p.depth[v] = v == p.src ? 0 : -1;
     p.parent[v] = v == p.src ? p.src : INT_MAX;
   }
+  // the caller's CSR: offsets non-decreasing within [0, nnz], columns in [0, n);
+  // anything else ends the run with BFS_ERR_INVALID before a row is read
+  bool bad = false;
+  for (int64_t v = gtid; v < p.n; v += gth) {
+    const int64_t o0 = p.off[v], o1 = p.off[v + 1];
+    bad |= o0 < 0 || o0 > o1 || o1 > p.nnz;
+  }
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0) atomicExch(&h->err, ((p.epoch & 0x0FFFFFFFu) << 4) | (unsigned)(-BFS_ERR_INVALID));
+  } else {
+    for (int64_t j = gtid; j < p.nnz; j += gth) {
+      const int c = p.col[j];
+      bad |= c < 0 || c >= p.n;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+      atomicExch(&h->err, ((p.epoch & 0x0FFFFFFFu) << 4) | (unsigned)(-BFS_ERR_INVALID));
+  }
+  if (!st_sync(p, h)) return;
   const long long sdeg = (long long)(p.off[p.src + 1] - p.off[p.src]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     h->n_f[0] = h->n_f[1] = h->m_f[0] = h->m_f[1] = 0;
@@ -149,47 +177,92 @@ __device__ void st_body(const StaticParams& p) {
     const int dir = s_dir;
     unsigned long long nf = 0, mf = 0;
     if (dir == 0) {
-      // forward: the set bits of F, 32 at a time per warp; each lane walks its row
+      // forward: the set bits of F, 32 words per warp (lane i owns word i); a
+      // lane walks a short row alone, the warp walks long rows together
       for (int64_t w0 = gwarp * 32; w0 < W; w0 += nwarps * 32) {
         const int64_t w = w0 + lane;
         unsigned fb = w < W ? F[w] : 0u;
         while (__any_sync(kFull, fb != 0)) {
           int u = -1;
+          int64_t b = 0, e = 0;
           if (fb) {
             u = (int)(w * 32 + __ffs(fb) - 1);
             fb &= fb - 1;
+            b = p.off[u];
+            e = p.off[u + 1];
           }
-          if (u >= 0) {
-            for (int64_t j = p.off[u]; j < p.off[u + 1]; ++j) {
-              const int v = p.col[j];
-              if ((V[v >> 5] >> (v & 31)) & 1u) continue;
-              atomicMin(p.parent + v, u);
-              atomicOr(N + (v >> 5), 1u << (v & 31));
+          const bool wide = u >= 0 && e - b > kStaticWarpRow;
+          if (u >= 0 && !wide)
+            for (int64_t j = b; j < e; ++j) st_push(p, V, N, u, p.col[j]);
+          for (unsigned lm = __ballot_sync(kFull, wide); lm; lm &= lm - 1) {
+            const int l = __ffs(lm) - 1;
+            const int uu = __shfl_sync(kFull, u, l);
+            const int64_t rb = __shfl_sync(kFull, b, l), re = __shfl_sync(kFull, e, l);
+            for (int64_t j0 = rb; j0 < re; j0 += 128) {  // four loads in flight per lane
+              int c[4];
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const int64_t j = j0 + lane + 32 * t;
+                c[t] = j < re ? p.col[j] : -1;
+              }
+#pragma unroll
+              for (int t = 0; t < 4; ++t)
+                if (c[t] >= 0) st_push(p, V, N, uu, c[t]);
             }
           }
         }
       }
     } else {
-      // backward: every unvisited vertex scans its sorted row to the first visited neighbour
-      for (int64_t w = gtid; w < W; w += gth) {
-        unsigned unv = ~V[w];
-        if (w == W - 1 && (p.n & 31)) unv &= (1u << (p.n & 31)) - 1u;
+      // backward: every unvisited vertex scans its sorted row to the first
+      // visited neighbour; 32 words per warp, long rows scanned by the warp
+      for (int64_t w0 = gwarp * 32; w0 < W; w0 += nwarps * 32) {
+        const int64_t w = w0 + lane;
+        unsigned unv = 0;
+        if (w < W) {
+          unv = ~V[w];
+          if (w == W - 1 && (p.n & 31)) unv &= (1u << (p.n & 31)) - 1u;
+        }
         unsigned found = 0;
-        while (unv) {
-          const int i = __ffs(unv) - 1;
-          unv &= unv - 1;
-          const int v = (int)(w * 32 + i);
-          const int64_t b = p.off[v], e = p.off[v + 1];
-          for (int64_t j = b; j < e; ++j) {
-            const int c = p.col[j];
-            if ((V[c >> 5] >> (c & 31)) & 1u) {
-              p.parent[v] = c;
-              p.depth[v] = L + 1;
-              found |= 1u << i;
-              nf += 1;
-              mf += (unsigned long long)(e - b);
-              break;
+        while (__any_sync(kFull, unv != 0)) {
+          int v = -1, i = 0, hit = -1;
+          int64_t b = 0, e = 0;
+          if (unv) {
+            i = __ffs(unv) - 1;
+            unv &= unv - 1;
+            v = (int)(w * 32 + i);
+            b = p.off[v];
+            e = p.off[v + 1];
+          }
+          const bool wide = v >= 0 && e - b > kStaticWarpRow;
+          if (v >= 0 && !wide)
+            for (int64_t j = b; j < e; ++j) {
+              const int c = p.col[j];
+              if ((V[c >> 5] >> (c & 31)) & 1u) {
+                hit = c;
+                break;
+              }
             }
+          for (unsigned lm = __ballot_sync(kFull, wide); lm; lm &= lm - 1) {
+            const int l = __ffs(lm) - 1;
+            const int64_t rb = __shfl_sync(kFull, b, l), re = __shfl_sync(kFull, e, l);
+            int h2 = -1;
+            for (int64_t j0 = rb; j0 < re; j0 += 32) {  // the first visited entry in row order
+              const int64_t j = j0 + lane;
+              const int c = j < re ? p.col[j] : -1;
+              const unsigned hb = __ballot_sync(kFull, c >= 0 && ((V[c >> 5] >> (c & 31)) & 1u));
+              if (hb) {
+                h2 = __shfl_sync(kFull, c, __ffs(hb) - 1);
+                break;
+              }
+            }
+            if (lane == l) hit = h2;
+          }
+          if (hit >= 0) {
+            p.parent[v] = hit;
+            p.depth[v] = L + 1;
+            found |= 1u << i;
+            nf += 1;
+            mf += (unsigned long long)(e - b);
           }
         }
         if (found) N[w] = found;
@@ -275,6 +348,18 @@ extern "C" int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_
   if ((int64_t)n > kStaticMaxVertices)
     return fail(BFS_ERR_OVERFLOW, "bfs_run_static supports at most 16777216 vertices (its fixed scratch size)");
   if (source < 0 || source >= n) return fail(BFS_ERR_INVALID, "source out of range");
+  {
+    const void* ptrs[4] = {row_off, col, depth, parent};
+    for (const void* q : ptrs) {
+      cudaPointerAttributes a;
+      if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BFS_ERR_INVALID, "bfs_run_static takes device pointers only");
+      }
+      if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(BFS_ERR_INVALID, "bfs_run_static takes device pointers only");
+    }
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -307,6 +392,7 @@ extern "C" int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_
   e = cudaMemcpyAsync(&nnz, row_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "read row_off[n]");
+  if (nnz < 0) return fail(BFS_ERR_INVALID, "row_off[n] is negative");
   p.off = row_off;
   p.col = col;
   p.depth = depth;
@@ -314,7 +400,9 @@ extern "C" int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_
   p.n = n;
   p.src = source;
   p.nnz = nnz;
-  p.timeout_ns = 2000ull * 1000000ull;
+  // every barrier wait is bounded: 2 s, plus 4 ns per row entry so that a valid
+  // graph with very long rows cannot reach the bound
+  p.timeout_ns = 2000ull * 1000000ull + 4ull * (unsigned long long)nnz;
   void* args[] = {&p};
   const int grid = g_static_dev[dev].grid;
   e = cudaLaunchCooperativeKernel((const void*)bfs_static_loop, dim3(grid), dim3(kStaticThreads), args, 0,
@@ -326,8 +414,10 @@ extern "C" int bfs_run_static(const int64_t* row_off, const int32_t* col, int32_
   if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static");
   if (err != 0 && (err >> 4) == p.epoch) {
     const int code = -(int)(err & 0xFu);
-    return fail(code, code == BFS_ERR_TIMEOUT ? "a device-side wait of bfs_run_static passed its deadline"
-                                              : "bfs_run_static reported an error");
+    return fail(code, code == BFS_ERR_TIMEOUT   ? "a device-side wait of bfs_run_static passed its deadline"
+                      : code == BFS_ERR_INVALID ? "bfs_run_static: row offsets not non-decreasing within "
+                                                  "[0, row_off[n]], or a column outside [0, n)"
+                                                : "bfs_run_static reported an error");
   }
   return BFS_OK;
 }
