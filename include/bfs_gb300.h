@@ -49,6 +49,14 @@ struct CUstream_st; /* cudaStream_t is `struct CUstream_st*` */
 #define BFS_SCHED_ALTERNATE 3 /* even levels forward, odd levels backward */
 #define BFS_SCHED_MASK 4      /* level L backward iff bit min(L,63) of schedule_mask is set */
 #define BFS_SCHED_PAPER 5     /* Sec. IV-B workload rule: FV vs factor * BV, BV = |U|(q+s)/q */
+#define BFS_SCHED_PAPER_SUBGRAPH 6 /* Sec. IV-B per subgraph: the dd, dn and nd visits each take their own
+                                      direction by the FV/BV rule with their own factor pair
+                                      (subgraph_factor0/1); nn is always forward.  Per subgraph X:
+                                      q = frontier vertices of X's source class with an X entry, FV =
+                                      their X entries, U = unvisited vertices of X's destination class
+                                      with an entry of the reversed subgraph, s = unvisited vertices of
+                                      X's source class with an X entry; a subgraph with q = 0 keeps its
+                                      direction.  Forward levels take atomicMin parents. */
 
 /* How a forward level picks the canonical parent of a newly reached vertex. */
 #define BFS_TD_PARENT_PULL 0      /* after the level, scan its sorted row for the first frontier neighbour */
@@ -74,11 +82,16 @@ typedef struct bfs_options {
   int32_t tuning;             /* bit 0: forward visits read the discovered word before an atomicOr;
                                  bit 1: record when the first and the last CTA finish each
                                  expansion (bfs_level_log t_first_done_ns / t_last_done_ns) */
+  double subgraph_factor0[3]; /* BFS_SCHED_PAPER_SUBGRAPH, for dd, dn, nd: forward->backward when
+                                 FV > factor0 * BV (default 0.5, 0.05, 1e-7, Sec. IV-B) */
+  double subgraph_factor1[3]; /* the same subgraphs: backward->forward when FV < factor1 * BV
+                                 (default 1e-7 each) */
   int32_t reserved[4];
 } bfs_options;
 
 /* Fills *opt with the defaults: th 64, host edges, Beamer alpha 15 / beta 18,
- * paper factors 0.5 / 1e-7, atomicMin parents, 2000 ms barrier bound, 60 s run bound. */
+ * paper factors 0.5 / 1e-7 (per subgraph 0.5 / 0.05 / 1e-7 and 1e-7), atomicMin
+ * parents, 2000 ms barrier bound, 60 s run bound. */
 int bfs_options_default(bfs_options* opt);
 
 typedef struct bfs_graph bfs_graph;
@@ -140,6 +153,9 @@ typedef struct bfs_level_log {
   uint64_t t_begin_ns, t_expand_ns, t_end_ns; /* device %globaltimer at the phase edges */
   uint64_t t_first_done_ns, t_last_done_ns;   /* when the first / last CTA finished the expansion
                                                  (with tuning bit 1; else 0) */
+  int32_t subgraph_directions; /* BFS_SCHED_PAPER_SUBGRAPH: bit 0 dd, bit 1 dn, bit 2 nd backward
+                                  (direction = 1 when any is); 0 otherwise */
+  int32_t reserved;
 } bfs_level_log;
 
 typedef struct bfs_stats {
@@ -351,6 +367,10 @@ int bfs_wait(bfs_graph* g, struct CUstream_st* stream);
  *   row_off[n+1] int64, col[row_off[n]] int32: caller-owned DEVICE memory, a
  *     symmetric CSR in the caller's ids with every row sorted ascending and no
  *     self-loops or repeated entries (the graph bfs_build_graph would build).
+ *     Checked on every call before any row is read: all four pointers are
+ *     device memory, the offsets are non-decreasing within [0, row_off[n]] and
+ *     every column lies in [0, n); otherwise BFS_ERR_INVALID.  Not checked:
+ *     sorted rows and symmetry (without them the parents need not be canonical).
  *   n: 1 .. 16,777,216 vertices; larger n returns BFS_ERR_OVERFLOW, nothing runs.
  *   depth[n], parent[n]: caller-owned DEVICE int32 buffers; same results as
  *     bfs_run (hop distance, canonical smallest-id parent, -1 unreached).

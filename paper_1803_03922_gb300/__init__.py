@@ -33,6 +33,7 @@ BFS_SCHED_BOTTOMUP = 2
 BFS_SCHED_ALTERNATE = 3
 BFS_SCHED_MASK = 4
 BFS_SCHED_PAPER = 5
+BFS_SCHED_PAPER_SUBGRAPH = 6
 
 BFS_TD_PARENT_PULL = 0
 BFS_TD_PARENT_ATOMICMIN = 1
@@ -47,7 +48,7 @@ class bfs_options(ctypes.Structure):
                 ("alpha", c_i32), ("beta", c_i32), ("factor0", c_dbl), ("factor1", c_dbl),
                 ("td_parent", c_i32), ("blocks_per_sm", c_i32), ("barrier_timeout_ms", c_i32),
                 ("test_skip_barrier", c_i32), ("run_timeout_ms", c_i32), ("tuning", c_i32),
-                ("reserved", c_i32 * 4)]
+                ("subgraph_factor0", c_dbl * 3), ("subgraph_factor1", c_dbl * 3), ("reserved", c_i32 * 4)]
 
 
 class bfs_graph_info(ctypes.Structure):
@@ -60,7 +61,8 @@ class bfs_level_log(ctypes.Structure):
     _fields_ = [("direction", c_i32), ("converted", c_i32), ("frontier", c_i64), ("frontier_edges", c_i64),
                 ("scanned", c_i64), ("edges_examined", c_i64), ("parent_edges", c_i64), ("found", c_i64),
                 ("queue_entries", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64),
-                ("t_first_done_ns", c_u64), ("t_last_done_ns", c_u64)]
+                ("t_first_done_ns", c_u64), ("t_last_done_ns", c_u64), ("subgraph_directions", c_i32),
+                ("reserved", c_i32)]
 
 
 class bfs_stats(ctypes.Structure):
@@ -400,7 +402,7 @@ class Graph:
         opt = bfs_options_default()
         opt.th = th
         for k, v in options.items():
-            setattr(opt, k, v)
+            setattr(opt, k, tuple(v) if isinstance(v, list) else v)
         self.opt = opt
         self._h = bfs_build_graph(src, dst, num_vertices, opt, stream)
         self.info = bfs_graph_get_info(self._h)
@@ -413,7 +415,7 @@ class Graph:
     def set_options(self, **options):
         opt = bfs_options_default()
         for k, v in options.items():
-            setattr(opt, k, v)
+            setattr(opt, k, tuple(v) if isinstance(v, list) else v)
         bfs_set_options(self._h, opt)
         opt.th, opt.edges_on_device = self.opt.th, self.opt.edges_on_device
         self.opt = opt

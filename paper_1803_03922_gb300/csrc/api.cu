@@ -57,7 +57,11 @@ int dmalloc(T** p, size_t count, int64_t* total, const char* what) {
 
 int check_options(const bfs_options& o) {
   if (o.th < 0) return fail(BFS_ERR_INVALID, "th must be >= 0");
-  if (o.schedule < BFS_SCHED_BEAMER || o.schedule > BFS_SCHED_PAPER) return fail(BFS_ERR_INVALID, "unknown schedule");
+  if (o.schedule < BFS_SCHED_BEAMER || o.schedule > BFS_SCHED_PAPER_SUBGRAPH)
+    return fail(BFS_ERR_INVALID, "unknown schedule");
+  for (int i = 0; i < 3; ++i)
+    if (!(o.subgraph_factor0[i] >= 0) || !(o.subgraph_factor1[i] >= 0))
+      return fail(BFS_ERR_INVALID, "subgraph factors must be >= 0");
   if (o.alpha <= 0 || o.beta <= 0) return fail(BFS_ERR_INVALID, "alpha and beta must be > 0");
   if (o.td_parent != BFS_TD_PARENT_PULL && o.td_parent != BFS_TD_PARENT_ATOMICMIN)
     return fail(BFS_ERR_INVALID, "unknown td_parent");
@@ -100,8 +104,9 @@ int alloc_run_state(bfs_graph* g) {
 }
 
 void free_all(bfs_graph* g) {
-  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->V, g->V1, g->N0, g->N1, g->depth_i,
-                  g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch};
+  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->lead, g->V, g->V1, g->N0, g->N1, g->depth_i,
+                  g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch,
+                  g->deg_del, g->sub_tot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (g->stage) cudaFree(g->stage);
@@ -200,6 +205,10 @@ extern "C" int bfs_options_default(bfs_options* opt) {
   opt->blocks_per_sm = 0;
   opt->barrier_timeout_ms = 2000;
   opt->run_timeout_ms = 60000;
+  opt->subgraph_factor0[0] = 0.5;
+  opt->subgraph_factor0[1] = 0.05;
+  opt->subgraph_factor0[2] = 1e-7;
+  for (int i = 0; i < 3; ++i) opt->subgraph_factor1[i] = 1e-7;
   return BFS_OK;
 }
 
@@ -309,6 +318,7 @@ static int fill_stats(bfs_graph* g, bfs_stats* st, const RunHeader& h) {
       o.t_end_ns = lg[L].t_end;
       o.t_first_done_ns = lg[L].t_first;
       o.t_last_done_ns = lg[L].t_last;
+      o.subgraph_directions = lg[L].subdirs;
       st->edges_examined += o.edges_examined;
     }
   }

@@ -40,11 +40,16 @@ struct __align__(64) LevelSlot {
   unsigned long long work2;     // hand-out counter of the deferred long rows
   unsigned long long nlong;     // deferred long rows (backward)
   unsigned long long pad[4];
+  // per-subgraph schedule, over this level's frontier: vertices that are delegates with a
+  // delegate neighbour, normal with a delegate neighbour, delegates with a normal neighbour;
+  // then the delegate neighbours of its delegates, their normal neighbours, and the delegate
+  // neighbours of its normal vertices (FV of dd, dn and nd)
+  unsigned long long sub[6];
 };
 constexpr int kSlots = 4;
 
 struct LevelLogDev {
-  int32_t dir, converted;
+  int32_t dir, converted, subdirs, pad;
   unsigned long long n_f, m_f, scanned, edges, fix_edges, found, qn;
   unsigned long long t_begin, t_expand, t_end, t_first, t_last;
 };
@@ -69,6 +74,7 @@ struct BfsParams {
   const int32_t* internal_of;// [n]
   const int4* head;          // [kHeadVecs n_ni]: first kHead neighbours (internal ids, -1 pad), then their caller ids
   const int32_t* deg;        // [n_ni] degree
+  const int2* lead;          // [n_ni] first row entry (internal id, -1 if none) and its caller id
   uint32_t* V;               // visited bitmaps, [words] each: level L reads one and writes
   uint32_t* V1;              // the other (depth <= L and depth <= L+1)
   uint32_t* N0;              // discovered-this-level bitmaps, [words] each
@@ -102,6 +108,11 @@ struct BfsParams {
   unsigned long long run_timeout_ns;
   int32_t out_vec4;          // out_depth/out_parent are 16-byte aligned
   int32_t tuning;            // bfs_options.tuning
+  // per-subgraph schedule: delegate neighbours per vertex [n_ni]; totals of the three vertex
+  // categories of LevelSlot::sub over the whole graph [3]; factors of dd, dn, nd
+  const int32_t* deg_del;
+  const unsigned long long* sub_tot;
+  double sf0[3], sf1[3];
 };
 
 }  // namespace bfsgb
@@ -122,6 +133,7 @@ struct bfs_graph {
   int32_t* internal_of = nullptr;
   int4* head = nullptr;
   int32_t* deg = nullptr;
+  int2* lead = nullptr;
   // run state
   uint32_t* V = nullptr;
   uint32_t* V1 = nullptr;
@@ -147,7 +159,10 @@ struct bfs_graph {
   cudaEvent_t ev_run[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr}, ev_join = nullptr;
   bfsgb::RunHeader* hdr_many = nullptr;  // pinned host copies of the run headers
   int64_t hdr_many_cap = 0;
+  int32_t* deg_del = nullptr;       // per-subgraph schedule (made on first use): delegate neighbours
+  unsigned long long* sub_tot = nullptr;  // and the three category totals
   int grid_blocks = 0;
+  int grid_blocks_sub = 0;         // CTAs of the per-subgraph build
   int variant = 2;                 // CTAs per SM of the level-loop build in use
   unsigned int epoch = 0;          // runs launched
 };

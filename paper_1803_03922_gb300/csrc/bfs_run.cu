@@ -58,17 +58,22 @@ __device__ void flush_block(Acc& a, unsigned long long* nf, unsigned long long* 
 // (vertices at depth <= L; read-only during level L, whose discoveries go to the
 // other buffer).  For an unvisited vertex (backward) or one found in level L
 // (parent pick after a forward level) a neighbour in Vc is at depth L exactly.
-template <bool kFix>
-__device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t* __restrict__ Vc) {
+// With kSub (per-subgraph directions), only neighbours of the classes in cls
+// count: bit 0 delegates, bit 1 normal vertices.
+template <bool kFix, bool kSub = false>
+__device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t* __restrict__ Vc, unsigned cls = 3u) {
+  if constexpr (kSub) {
+    if (!((c < p.d) ? (cls & 1u) : (cls & 2u))) return false;
+  }
   return (Vc[c >> 5] >> (c & 31)) & 1u;
 }
 
 // Whole-warp scan of row entries [from, end) of a row starting at rbeg, 128
 // entries (one 128-bit load per lane) per step; returns the first entry passing
 // the probe (or -1) and kv = its position in the row + 1 (or end - rbeg).
-template <bool kFix>
+template <bool kFix, bool kSub = false>
 __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t end,
-                         const uint32_t* __restrict__ Ncur, int64_t& kv) {
+                         const uint32_t* __restrict__ Ncur, int64_t& kv, unsigned cls = 3u) {
   const int lane = lane_id();
   for (int64_t j0 = from & ~(int64_t)3; j0 < end; j0 += 128) {
     const int64_t j = j0 + lane * 4;
@@ -80,7 +85,7 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
 #pragma unroll
       for (int t = 3; t >= 0; --t) {
         const int64_t idx = j + t;
-        if (idx >= from && idx < end && probe<kFix>(p, cs[t], Ncur)) {
+        if (idx >= from && idx < end && probe<kFix, kSub>(p, cs[t], Ncur, cls)) {
           best = (unsigned)(idx - rbeg);
           bc = cs[t];
         }
@@ -110,9 +115,9 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
 // vertex and row start go to the level's long-row list and hit becomes kDeferred.
 constexpr int kDeferred = -2;
 
-template <bool kFix>
+template <bool kFix, bool kSub = false>
 __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t end, const uint32_t* __restrict__ Ncur,
-                          int& hit, int64_t& k, int defer_v = -1, LevelSlot* defer_slot = nullptr) {
+                          int& hit, int64_t& k, int defer_v = -1, LevelSlot* defer_slot = nullptr, unsigned cls = 3u) {
   constexpr int G = kTailLanes, P = kTailPerLane, R = 32 / G, S = G * P;
   static_assert(G == 2 || G == 4 || G == 8 || G == 16, "group scan: 2, 4, 8 or 16 lanes per row");
   static_assert(P == 1 || P == 2 || P == 4, "group scan: 1 entry, or one 64- or 128-bit load per lane");
@@ -129,6 +134,8 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
     const int srcl = (g < take) ? (__ffs(r) - 1) : 0;
     const int64_t rbeg = __shfl_sync(kFull, beg, srcl);
     const int64_t rend = __shfl_sync(kFull, end, srcl);
+    // the group probes with the row owner's classes (kSub), not its own
+    const unsigned gcls = kSub ? __shfl_sync(kFull, cls, srcl) : cls;
     const int64_t from = rbeg + kHead;
     bool gdone = g >= take;
     int ghit = -1;
@@ -142,7 +149,7 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
       if (!gdone && j < rend) {
         if constexpr (P == 1) {
           const int c1 = p.col[j];
-          if (probe<kFix>(p, c1, Ncur)) c = c1;
+          if (probe<kFix, kSub>(p, c1, Ncur, gcls)) c = c1;
         } else {
           int cs[P];
           if constexpr (P == 4) {
@@ -158,7 +165,7 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
           }
           bool hh[P];
 #pragma unroll
-          for (int t = 0; t < P; ++t) hh[t] = j + t >= from && j + t < rend && probe<kFix>(p, cs[t], Ncur);
+          for (int t = 0; t < P; ++t) hh[t] = j + t >= from && j + t < rend && probe<kFix, kSub>(p, cs[t], Ncur, gcls);
 #pragma unroll
           for (int t = P - 1; t >= 0; --t)
             if (hh[t]) {
@@ -213,8 +220,9 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
     lrem &= lrem - 1;
     const int64_t rbeg = __shfl_sync(kFull, beg, owner);
     const int64_t rend = __shfl_sync(kFull, end, owner);
+    const unsigned ocls = kSub ? __shfl_sync(kFull, cls, owner) : cls;
     int64_t k2;
-    const int h2 = warp_scan<kFix>(p, rbeg, rbeg + kHead, rend, Ncur, k2);
+    const int h2 = warp_scan<kFix, kSub>(p, rbeg, rbeg + kHead, rend, Ncur, k2, ocls);
     if (lane == owner) {
       hit = h2;
       k = k2;
@@ -265,14 +273,14 @@ __device__ __forceinline__ HeadRec head_load(const BfsParams& p, bool act, int v
 
 // Probes the head entries of a loaded record: first hit (internal id, caller
 // id) and k = its position + 1, or k = min(degree, kHead) and hit = -1.
-template <bool kFix>
+template <bool kFix, bool kSub = false>
 __device__ __forceinline__ void head_probe(const BfsParams& p, const HeadRec& h, const uint32_t* __restrict__ Ncur,
-                                           int& hit, int& cid, int64_t& k) {
+                                           int& hit, int& cid, int64_t& k, unsigned cls = 3u) {
   const int* nb = h.nb;
   const int* cs = h.cid;
   bool hh[kHead];
 #pragma unroll
-  for (int t = 0; t < kHead; ++t) hh[t] = nb[t] >= 0 && probe<kFix>(p, nb[t], Ncur);
+  for (int t = 0; t < kHead; ++t) hh[t] = nb[t] >= 0 && probe<kFix, kSub>(p, nb[t], Ncur, cls);
   hit = -1;
   cid = -1;
   k = h.deg < kHead ? h.deg : kHead;
@@ -287,17 +295,17 @@ __device__ __forceinline__ void head_probe(const BfsParams& p, const HeadRec& h,
 
 // Phases B/C for the lanes whose row continues past the head entries without a
 // hit: loads the row offset and finishes the scan (warp-collective).
-template <bool kFix>
+template <bool kFix, bool kSub = false>
 __device__ __forceinline__ void pull_tail(const BfsParams& p, bool act, int v, int deg,
                                           const uint32_t* __restrict__ Ncur, int& hit, int& cid, int64_t& k,
-                                          LevelSlot* defer_slot = nullptr) {
+                                          LevelSlot* defer_slot = nullptr, unsigned cls = 3u) {
   const bool more = act && hit < 0 && deg > kHead;
   int64_t beg = 0, end = 0;
   if (more) {
     beg = p.off[v];
     end = beg + deg;
   }
-  pull_rest<kFix>(p, more, beg, end, Ncur, hit, k, v, defer_slot);
+  pull_rest<kFix, kSub>(p, more, beg, end, Ncur, hit, k, v, defer_slot, cls);
   if (more && hit >= 0) cid = p.caller_of[hit];
 }
 
@@ -321,52 +329,50 @@ __device__ int pull_head(const BfsParams& p, bool act, int v, const uint32_t* __
 
 // ---- forward level ------------------------------------------------------------------------
 
-// One row entry u->v of a forward visit (v < 0: lane idle).  An unvisited target
-// gets its bit in N (fire-and-forget atomicOr); with atomicMin parents, the
-// frontier vertex's caller id is also offered to v's parent slot.  Which lane
-// set the bit does not matter: the level end builds the next frontier from N.
-__device__ __forceinline__ void td_edge(const BfsParams& p, const uint32_t* __restrict__ Vc, int v, int pcaller,
-                                        uint32_t* __restrict__ N, bool& found) {
-  if (v < 0) return;
-  const unsigned w = (unsigned)v >> 5, bit = 1u << (v & 31);
-  if (Vc[w] & bit) return;
-  found = true;
-  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, pcaller);
-  if (!(p.tuning & 1) || !(__ldcg(N + w) & bit)) atomicOr(N + w, bit);
-}
-
 // Four row entries of one lane: the four visited-bit probes are issued before
 // any reduction, so they are in flight together.
+template <bool kSub = false>
 __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __restrict__ Vc, const int (&v)[4],
-                                         int pcaller, uint32_t* __restrict__ N, bool& found) {
+                                         int pcaller, uint32_t* __restrict__ N, bool& found, unsigned allow = 3u) {
   unsigned vw[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? Vc[(unsigned)v[t] >> 5] : kFull;
+  // consecutive row entries often fall in one bitmap word (delegates are numbered in
+  // caller order, and rows are sorted by caller id): their discovered bits are
+  // OR-ed together and set with one atomic per run of equal words
+  unsigned rw = 0xFFFFFFFFu, rb = 0u;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
+    if constexpr (kSub) {
+      if (!((v[t] < p.d) ? (allow & 1u) : (allow & 2u))) continue;
+    }
     found = true;
     if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], pcaller);
-    uint32_t* nw = N + ((unsigned)v[t] >> 5);
-    const unsigned bit = 1u << (v[t] & 31);
-    if (!(p.tuning & 1) || !(__ldcg(nw) & bit)) atomicOr(nw, bit);
+    const unsigned w = (unsigned)v[t] >> 5, bit = 1u << (v[t] & 31);
+    if (w != rw) {
+      if (rb) atomicOr(N + rw, rb);
+      rw = w;
+      rb = 0u;
+    }
+    if (!(p.tuning & 1) || !(__ldcg(N + w) & bit)) rb |= bit;
   }
+  if (rb) atomicOr(N + rw, rb);
 }
 
 // 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
 // concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
 // whose inclusive degree prefix first exceeds e).
+template <bool kSub = false>
 __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, const int32_t* __restrict__ Qc,
-                         int64_t qn, int64_t b, uint32_t* __restrict__ N, bool& found) {
+                         int64_t qn, int64_t b, uint32_t* __restrict__ N, bool& found, unsigned allow = 3u) {
   const int lane = lane_id();
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
   int64_t beg = 0, deg = 0;
-  int pc = 0;
   if (u >= 0) {
     beg = p.off[u];
     deg = p.deg[u];
-    if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) pc = p.caller_of[u];
   }
   const int64_t incl = warp_incl_scan(deg);
   const int64_t total = __shfl_sync(kFull, incl, 31);
@@ -381,14 +387,27 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
     }
     const int64_t ob = __shfl_sync(kFull, beg, pos);
     const int64_t ox = __shfl_sync(kFull, excl, pos);
-    const int opc = __shfl_sync(kFull, pc, pos);
-    td_edge(p, Vc, e < total ? p.col[ob + (e - ox)] : -1, opc, N, found);
+    const int ou = __shfl_sync(kFull, u, pos);
+    int v = e < total ? p.col[ob + (e - ox)] : -1;
+    if constexpr (kSub) {  // per-subgraph directions: only targets of the classes in allow
+      if (v >= 0 && !((v < p.d) ? (allow & 1u) : (allow & 2u))) v = -1;
+    }
+    // the frontier vertex's caller id is loaded only for an edge into an unvisited
+    // target (most edges of a late forward level meet visited vertices)
+    if (v >= 0 && !((Vc[(unsigned)v >> 5] >> (v & 31)) & 1u)) {
+      found = true;
+      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, p.caller_of[ou]);
+      const unsigned bit = 1u << (v & 31);
+      uint32_t* nw = N + ((unsigned)v >> 5);
+      if (!(p.tuning & 1) || !(__ldcg(nw) & bit)) atomicOr(nw, bit);
+    }
   }
 }
 
 // One kChunk-entry piece of a delegate's row, 128-bit loads.
+template <bool kSub = false>
 __device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, int2 ck, uint32_t* __restrict__ N,
-                         bool& found) {
+                         bool& found, unsigned allow = 3u) {
   const int lane = lane_id();
   const int u = ck.x;
   const int64_t rb = p.off[u], re = p.off[u + 1];
@@ -404,11 +423,11 @@ __device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, in
     if (ja < end) {
       const int v[4] = {ja >= beg ? ca.x : -1, (ja + 1 >= beg && ja + 1 < end) ? ca.y : -1,
                         (ja + 2 >= beg && ja + 2 < end) ? ca.z : -1, (ja + 3 >= beg && ja + 3 < end) ? ca.w : -1};
-      td_edge4(p, Vc, v, pc, N, found);
+      td_edge4<kSub>(p, Vc, v, pc, N, found, allow);
     }
     if (jb < end) {
       const int v[4] = {cb.x, jb + 1 < end ? cb.y : -1, jb + 2 < end ? cb.z : -1, jb + 3 < end ? cb.w : -1};
-      td_edge4(p, Vc, v, pc, N, found);
+      td_edge4<kSub>(p, Vc, v, pc, N, found, allow);
     }
   }
 }
@@ -440,7 +459,11 @@ struct WorkCursor {
 // Work items of a forward level: the delegate chunks of F_L, then the normal
 // queue in batches of 32; warp w takes items w, w + warps, ... (a shared counter
 // measured slower here: the chunks are uniform).
-__device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, bool& found) {
+// With kSub, allow_n / allow_d are the target classes that normal / delegate
+// frontier vertices push to (bit 0 delegates, bit 1 normal vertices).
+template <bool kSub = false>
+__device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, bool& found,
+                          unsigned allow_n = 3u, unsigned allow_d = 3u) {
   const LevelSlot* sc = p.slot + (L & (kSlots - 1));
   const int64_t qn = (int64_t)__ldcg(&sc->qn);
   const int64_t nch = (int64_t)__ldcg(&sc->nch);
@@ -451,10 +474,11 @@ __device__ void expand_td(const BfsParams& p, const uint32_t* __restrict__ Vc, i
   const int64_t gwarp = spread_warp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t it = gwarp; it < total; it += nwarps) {
-    if (it < nch)
-      td_chunk(p, Vc, CLc[it], N, found);
-    else
-      td_batch(p, Vc, Qc, qn, it - nch, N, found);
+    if (it < nch) {
+      if (!kSub || allow_d) td_chunk<kSub>(p, Vc, CLc[it], N, found, allow_d);
+    } else {
+      td_batch<kSub>(p, Vc, Qc, qn, it - nch, N, found, allow_n);
+    }
   }
 }
 
@@ -615,14 +639,146 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
   return deferred;
 }
 
+// Words of a dense backward item handled per step (their lead records are in
+// flight together).
+constexpr int kDenseStep = 4;
+
+// Settles the pending vertices pend[0..cnt) (cnt <= 32, one per lane) of a dense
+// backward item: their first entry missed, so they scan on from the full head
+// record and the row tail, exactly as the sparse items do; found vertices get
+// depth and parent and their bit in the warp's found words (item-relative).
+__device__ bool bu_settle(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, int64_t w0, const int* pend,
+                          int cnt, unsigned* found, LevelSlot* sc, Acc& acc) {
+  const int lane = lane_id();
+  const bool act = lane < cnt;
+  const int v = act ? pend[lane] : 0;
+  const HeadRec h = head_load(p, act, v);
+  int hit = -1, cid = -1;
+  int64_t k = 0;
+  if (act) head_probe<false>(p, h, Vc, hit, cid, k);
+  pull_tail<false>(p, act, v, h.deg, Vc, hit, cid, k, sc);
+  bool deferred = false;
+  if (act) {
+    if (hit == kDeferred) {
+      deferred = true;
+    } else {
+      acc.scanned += 1;
+      acc.edges += (unsigned long long)k;
+      if (hit >= 0) {
+        p.parent_i[v] = cid;
+        p.depth_i[v] = L + 1;
+        acc.nf += 1;
+        acc.mf += (unsigned long long)h.deg;
+        atomicOr(found + ((v >> 5) - w0), 1u << (v & 31));
+      }
+    }
+  }
+  __syncwarp();
+  return __any_sync(kFull, deferred);
+}
+
+// A dense backward item (most vertices unvisited): bitmap words [w0, w0+iw),
+// iw a multiple of kDenseStep up to 32.
+// The 32 vertices of a word go to the 32 lanes (lane = bit), kDenseStep words
+// per step: every unvisited vertex loads its lead record (first entry and its
+// caller id; a warp reads 256 contiguous bytes per word) and degree, and probes
+// the first entry.  A hit settles the vertex (canonical parent: the first entry
+// in caller order); a miss with more entries joins the warp's pending list,
+// settled 32 at a time by bu_settle.  No compaction, no per-vertex search.
+__device__ bool bu_dense_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
+                              uint32_t* __restrict__ Nclr, int L, int64_t w0, int iw, unsigned* found, int* pend,
+                              uint32_t* __restrict__ N, LevelSlot* sc, Acc& acc, LevelSlot* qslot) {
+  bool deferred = false;
+  const int lane = lane_id();
+  const int64_t W = p.words;
+  const int tail = p.n_ni & 31;
+  const int64_t wl = w0 + lane;
+  const bool own = lane < iw && wl < W;  // this lane's word belongs to the item
+  unsigned vraw = 0, vis = kFull;
+  if (own) {
+    vraw = Vc[wl];
+    vis = vraw;
+    if (wl == W - 1 && tail) vis |= ~((1u << tail) - 1u);
+  }
+  unsigned fword = 0;  // first-entry hits of word w0 + lane
+  int npend = 0;       // warp-uniform
+  for (int s0 = 0; s0 < iw; s0 += kDenseStep) {
+    int2 a[kDenseStep];
+    int dg[kDenseStep];
+    bool un[kDenseStep];
+#pragma unroll
+    for (int u = 0; u < kDenseStep; ++u) {
+      un[u] = !((__shfl_sync(kFull, vis, s0 + u) >> lane) & 1u);
+      const int v = (int)((w0 + s0 + u) * 32 + lane);
+      a[u] = un[u] ? __ldg(p.lead + v) : make_int2(-1, -1);
+      dg[u] = un[u] ? __ldg(p.deg + v) : 0;
+    }
+    unsigned pw[kDenseStep];
+#pragma unroll
+    for (int u = 0; u < kDenseStep; ++u) pw[u] = a[u].x >= 0 ? Vc[a[u].x >> 5] : 0u;
+#pragma unroll
+    for (int u = 0; u < kDenseStep; ++u) {
+      const int v = (int)((w0 + s0 + u) * 32 + lane);
+      const bool h0 = un[u] && a[u].x >= 0 && ((pw[u] >> (a[u].x & 31)) & 1u);
+      const bool more = un[u] && !h0 && dg[u] > 1;
+      if (h0) {
+        p.parent_i[v] = a[u].y;
+        p.depth_i[v] = L + 1;
+        acc.nf += 1;
+        acc.mf += (unsigned long long)dg[u];
+      }
+      if (un[u] && !more) {  // settled here: a first-entry hit, or a one-entry row that missed
+        acc.scanned += 1;
+        acc.edges += 1;
+      }
+      const unsigned hb = __ballot_sync(kFull, h0);
+      if (lane == s0 + u) fword = hb;
+      const unsigned mb = __ballot_sync(kFull, more);
+      if (more) pend[npend + __popc(mb & ((1u << lane) - 1u))] = v;
+      npend += __popc(mb);
+    }
+    // settle full batches once the step's records are dead (pend holds < 32 before the step)
+    int done = 0;
+    for (; npend - done >= 32; done += 32) {
+      __syncwarp();
+      deferred |= bu_settle(p, Vc, L, w0, pend + done, 32, found, sc, acc);
+    }
+    if (done) {
+      const int rest = npend - done;
+      const int x = lane < rest ? pend[done + lane] : 0;
+      __syncwarp();
+      if (lane < rest) pend[lane] = x;
+      __syncwarp();
+      npend = rest;
+    }
+  }
+  if (npend > 0) {
+    __syncwarp();
+    deferred |= bu_settle(p, Vc, L, w0, pend, npend, found, sc, acc);
+  }
+  __syncwarp();
+  unsigned f = 0u;
+  if (own) {
+    f = fword | found[lane];
+    N[wl] = f;
+    Vn[wl] = vraw | f;
+    Nclr[wl] = 0u;
+  }
+  found[lane] = 0u;
+  if (qslot) append_next(p, wl * 32, f, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, qslot);
+  __syncwarp();
+  return deferred;
+}
+
 // A backward level: items of iw bitmap words (iw = 4..32, larger when few
 // vertices are left), split statically; rows still unsettled after kHead +
 // kShort entries are deferred to the level's long-row list, which all warps then
 // drain with dynamic hand-out, one row per warp and 128-bit loads, so that long
 // scans spread over the grid instead of stalling the warp that met them.
 __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
-                          uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc, bool build_next) {
+                          uint32_t* __restrict__ Nclr, int L, int iw, Acc& acc, bool build_next, bool dense) {
   __shared__ unsigned s_found[kMaxWarpsPerBlock][32];
+  __shared__ int s_pend[kMaxWarpsPerBlock][32 * (kDenseStep + 1)];
   uint32_t* N = (L & 1) ? p.N1 : p.N0;
   const int lane = lane_id();
   unsigned* found = s_found[threadIdx.x >> 5];
@@ -635,9 +791,87 @@ __device__ bool expand_bu(const BfsParams& p, const uint32_t* __restrict__ Vc, u
   const int64_t nitems = (W + iw - 1) / iw;
   bool deferred = false;
   LevelSlot* qslot = build_next ? p.slot + ((L + 1) & (kSlots - 1)) : nullptr;
+  if (dense) {
+    // items of 32 words, narrower (down to kDenseStep) until every warp has two
+    int iwd = 32;
+    while (iwd > kDenseStep && (W + iwd - 1) / iwd < 2 * nwarps) iwd >>= 1;
+    int* pend = s_pend[threadIdx.x >> 5];
+    for (int64_t it = gwarp; it * iwd < W; it += nwarps)
+      deferred |= bu_dense_item(p, Vc, Vn, Nclr, L, it * iwd, iwd, found, pend, N, sc, acc, qslot);
+    return deferred;
+  }
   for (int64_t it = gwarp; it < nitems; it += nwarps)
     deferred |= bu_item(p, Vc, Vn, Nclr, L, it * iw, iw, found, N, sc, acc, qslot);
   return deferred;
+}
+
+// Backward pulls under per-subgraph directions (Sec. IV-B): an unvisited
+// delegate pulls from the classes whose subgraph into the delegates is backward
+// (cls_del: bit 0 dd, from delegates; bit 1 nd, from normal vertices), an
+// unvisited normal vertex from the delegates when dn is backward (cls_norm bit
+// 0).  The scan stops at the first neighbour of an allowed class in the
+// visited bitmap; that neighbour is the smallest-id parent among those classes.
+// A forward push of the same level may offer other parents, so the hit is
+// offered by atomicMin and marked in N by atomicOr; the level end writes the
+// depth.  Items of 32 bitmap words, 32 unvisited vertices per step.
+__device__ void expand_bu_sub(const BfsParams& p, const uint32_t* __restrict__ Vc, int L, unsigned cls_del,
+                              unsigned cls_norm, Acc& acc, bool& found) {
+  uint32_t* N = (L & 1) ? p.N1 : p.N0;
+  const int lane = lane_id();
+  const int64_t W = cls_norm ? p.words : min(p.words, ((int64_t)p.d + 31) / 32);
+  const int tail = p.n_ni & 31;
+  const int64_t gwarp = spread_warp();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = gwarp * 32; w0 < W; w0 += nwarps * 32) {
+    const int64_t w = w0 + lane;
+    unsigned unv = 0;
+    if (w < W) {
+      unsigned vis = Vc[w];
+      if (w == p.words - 1 && tail) vis |= ~((1u << tail) - 1u);
+      const int64_t v0 = w * 32;
+      unsigned dmask = 0;  // delegate bits of this word
+      if (v0 < p.d) dmask = (p.d - v0 >= 32) ? kFull : ((1u << (p.d - v0)) - 1u);
+      unv = ~vis & ((cls_del ? dmask : 0u) | (cls_norm ? ~dmask : 0u));
+    }
+    const int cnt = __popc(unv);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(kFull, incl, 31);
+    const int excl = incl - cnt;
+    for (int b = 0; b < total; b += 32) {
+      const int k = b + lane;
+      int j = 0;
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int t = __shfl_sync(kFull, incl, j + sh - 1);
+        if (t <= k) j += sh;
+      }
+      const unsigned m = __shfl_sync(kFull, unv, j);
+      const int ex = __shfl_sync(kFull, excl, j);
+      const bool act = k < total;
+      const int bit = act ? nth_set_bit(m, k - ex) : 0;
+      const int v = (int)((w0 + j) * 32 + bit);
+      const unsigned cls = v < p.d ? cls_del : (cls_norm ? 1u : 0u);
+      const HeadRec h = head_load(p, act, v);
+      int hit = -1, cid = -1;
+      int64_t kv = 0;
+      if (act) head_probe<false, true>(p, h, Vc, hit, cid, kv, cls);
+      pull_tail<false, true>(p, act, v, h.deg, Vc, hit, cid, kv, nullptr, cls);
+      if (act) {
+        acc.scanned += 1;
+        acc.edges += (unsigned long long)kv;
+        if (hit >= 0) {
+          atomicMin(p.parent_i + v, cid);
+          atomicOr(N + (v >> 5), 1u << (v & 31));
+          found = true;
+        }
+      }
+    }
+  }
 }
 
 // Second half of a backward level, between two grid barriers (so the long-row
@@ -694,10 +928,44 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
 // search over the lanes' prefixes, bit by rank within the word).  With `merge`,
 // also writes the next visited bitmap Vn = Vc | Nsrc and clears Nclr.  With `count` (after a forward level),
 // also writes depth `depth` for every new vertex and adds n_f and m_f.
+// Counters of the per-subgraph schedule over a set of vertices (LevelSlot::sub).
+struct SubAcc {
+  unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+};
+
+__device__ __forceinline__ void sub_count(const BfsParams& p, int v, int deg, SubAcc& a) {
+  const int dd = p.deg_del[v], dn = deg - dd;
+  if (v < p.d) {
+    a.c[0] += dd > 0;
+    a.c[2] += dn > 0;
+    a.c[3] += (unsigned long long)dd;
+    a.c[4] += (unsigned long long)dn;
+  } else {
+    a.c[1] += dd > 0;
+    a.c[5] += (unsigned long long)dd;
+  }
+}
+
+// Adds every thread's SubAcc into slot->sub with one atomic per CTA and counter.
+__device__ void flush_sub(SubAcc& a, LevelSlot* slot) {
+  __shared__ unsigned long long s_sub[6];
+  if (threadIdx.x < 6) s_sub[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const unsigned long long x = warp_sum(a.c[i]);
+    if (lane_id() == 0 && x) atomicAdd(&s_sub[i], x);
+  }
+  __syncthreads();
+  if (threadIdx.x < 6 && s_sub[threadIdx.x]) atomicAdd(&slot->sub[threadIdx.x], s_sub[threadIdx.x]);
+  a = SubAcc();
+}
+
+template <bool kSub = false>
 __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restrict__ Vc, uint32_t* __restrict__ Vn,
                                      const uint32_t* __restrict__ Nsrc, uint32_t* __restrict__ Nclr,
                                      int32_t* __restrict__ Q, int2* __restrict__ CL, LevelSlot* slot, bool merge,
-                                     bool count, int depth, Acc& acc) {
+                                     bool count, int depth, Acc& acc, SubAcc* sacc = nullptr) {
   const int64_t W = p.words;
   const int lane = lane_id();
   const int64_t gwarp = spread_warp();
@@ -762,6 +1030,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
           p.depth_i[v] = depth;
           acc.nf += 1;
           acc.mf += (unsigned long long)dg;
+          if constexpr (kSub) sub_count(p, v, dg, *sacc);
         }
         if (v >= p.d)
           Q[qbase + nex + __popc(m & ~dm & ((1u << bit) - 1u))] = v;
@@ -922,6 +1191,20 @@ __device__ int decide(const BfsParams& p, int L1, int cur, unsigned long long nf
   }
 }
 
+// One subgraph's direction for the next level under the per-subgraph schedule
+// (Sec. IV-B): q frontier vertices of its source class with an entry in it, fv
+// those entries, U unvisited vertices of its destination class with an entry
+// of the reversed subgraph, su unvisited vertices of its source class with an
+// entry; BV = U (q + su) / q in double.  With q = 0 there is nothing to visit
+// and the direction is kept.
+__device__ __forceinline__ int sub_rule(int cur, unsigned long long q, unsigned long long fv, long long U, long long su,
+                                        double f0, double f1) {
+  if (q == 0) return cur;
+  const double qd = (double)q, sd = (double)(su > 0 ? su : 0), fvd = (double)fv;
+  const double bv = (double)(U > 0 ? U : 0) * (qd + sd) / qd;
+  return cur == 0 ? (fvd > f0 * bv ? 1 : 0) : (fvd < f1 * bv ? 0 : 1);
+}
+
 // Spread of the CTAs' finishing times of an expansion (the tracing option).
 __device__ void trace_done(LevelSlot* sc) {
   __syncthreads();
@@ -932,14 +1215,16 @@ __device__ void trace_done(LevelSlot* sc) {
   }
 }
 
+template <bool kSub>
 __device__ void run_body(const BfsParams& p);
 
 
-// Two builds of the same kernel: 2 CTAs of 512 threads per SM (64 registers) or
-// 3 (40 registers, some spilled to local memory).
-template <int kMinBlocks, int kThr>
+// Builds of the same kernel: 2 CTAs of 512 threads per SM (64 registers) or
+// 3 (40 registers, some spilled to local memory), one of 1024; kSub: the
+// per-subgraph direction schedule (BFS_SCHED_PAPER_SUBGRAPH).
+template <int kMinBlocks, int kThr, bool kSub = false>
 __global__ void __launch_bounds__(kThr, kMinBlocks) bfs_level_loop(BfsParams p) {
-  run_body(p);
+  run_body<kSub>(p);
 }
 
 // Bits a barrier's master hands to every CTA.
@@ -948,6 +1233,12 @@ constexpr int kBitBackward = 1, kBitDone = 2, kBitConvert = 4, kBitDrain = 8;
 constexpr int kBitLists = 64;
 // arrival flag of a forward expansion's barrier: the CTA met an unvisited target
 constexpr int kFlagFound = 16;
+// a backward level with at least half of the non-isolated vertices unvisited
+// takes the dense items (bu_dense_item)
+constexpr int kBitDense = 128;
+__device__ __forceinline__ int dense_bit(long long unvisited, const BfsParams& p) {
+  return (!(p.tuning & 4) && unvisited * 2 >= (long long)p.n_ni) ? kBitDense : 0;
+}
 // Item width 4 << c words of a backward level: about 64 unvisited vertices per
 // item, or 128 when under 1/64 of the vertices are delegates (a graph of
 // near-uniform degree, whose rows cost alike, so wider items lose no balance).
@@ -958,9 +1249,20 @@ __device__ __forceinline__ int iw_code(long long unvisited, const BfsParams& p) 
   return c << 4;
 }
 
+// Bits of the per-subgraph schedule's directions in the barrier word (the
+// single-direction bits they reuse have no meaning in that schedule).
+constexpr int kBitSubDD = kBitBackward, kBitSubDN = kBitDrain, kBitSubND = kBitLists;
+
+__device__ __forceinline__ unsigned sub_dirs(int bits) {
+  return ((bits & kBitSubDD) ? 1u : 0u) | ((bits & kBitSubDN) ? 2u : 0u) | ((bits & kBitSubND) ? 4u : 0u);
+}
+
+template <bool kSub>
 __device__ void run_body(const BfsParams& p) {
   // state of the direction decision, kept by CTA 0 (the barriers' master)
   __shared__ long long s_mu, s_unv;
+  // per-subgraph schedule: unvisited vertices of the three categories of LevelSlot::sub
+  __shared__ long long s_su[3];
   __shared__ unsigned long long s_prev_nf, s_reach_e, s_reach_v, s_tb, s_te, s_tnf, s_log[5];
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
@@ -989,7 +1291,7 @@ __device__ void run_body(const BfsParams& p) {
     reinterpret_cast<uint4*>(p.N0)[q] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(p.N1)[q] = make_uint4(0, 0, 0, 0);
   }
-  if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
+  if (kSub || p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
     const int64_t P4 = ((int64_t)p.n_ni + 3) / 4;
     for (int64_t q = gtid; q < P4; q += gthreads) {
       int4 x = make_int4(INT_MAX, INT_MAX, INT_MAX, INT_MAX);
@@ -1032,10 +1334,25 @@ __device__ void run_body(const BfsParams& p) {
     s_reach_v = 1;
   }
   if (p.test_skip_barrier && blockIdx.x == 0) return;  // the others' bounded wait must expire
-  int bits = grid_sync(p, seq, [&](int) {
-    return (src_in ? 0 : kBitDone) | (decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv) ? kBitBackward : 0) |
-           iw_code(s_unv, p);
-  });
+  int bits;
+  if constexpr (kSub) {
+    // level 0 from F_0 = {s}, every subgraph forward before it
+    bits = grid_sync(p, seq, [&](int) {
+      if (!src_in) return kBitDone;
+      SubAcc a;
+      sub_count(p, src_i, (int)src_deg, a);
+      for (int i = 0; i < 3; ++i) s_su[i] = (long long)p.sub_tot[i] - (long long)a.c[i];
+      const int dd = sub_rule(0, a.c[0], a.c[3], s_su[0], s_su[0], p.sf0[0], p.sf1[0]);
+      const int dn = sub_rule(0, a.c[2], a.c[4], s_su[1], s_su[2], p.sf0[1], p.sf1[1]);
+      const int nd = sub_rule(0, a.c[1], a.c[5], s_su[2], s_su[1], p.sf0[2], p.sf1[2]);
+      return (dd ? kBitSubDD : 0) | (dn ? kBitSubDN : 0) | (nd ? kBitSubND : 0) | iw_code(s_unv, p);
+    });
+  } else {
+    bits = grid_sync(p, seq, [&](int) {
+      return (src_in ? 0 : kBitDone) | (decide(p, 0, 0, 1, src_deg, 1, s_mu, s_unv) ? kBitBackward : 0) |
+             iw_code(s_unv, p) | dense_bit(s_unv, p);
+    });
+  }
   if (bits < 0) return;
 
   const unsigned long long t_start = gtimer();
@@ -1049,6 +1366,92 @@ __device__ void run_body(const BfsParams& p) {
     // run's deadline.  A failure set here ends every CTA at its next barrier.
     if (threadIdx.x == 0 && (L > p.n_ni + 1 || gtimer() - t_start > p.run_timeout_ns))
       set_failed(p, BFS_ERR_TIMEOUT);
+    if constexpr (kSub) {
+      // Per-subgraph directions (Sec. IV-B): nn forward always; dd, dn, nd as decided.
+      // One phase pushes from the frontier lists to the allowed target classes and
+      // pulls for the unvisited vertices of the backward subgraphs; the level end
+      // builds the next lists, depths and counters.
+      const unsigned sd = sub_dirs(bits);
+      LevelSlot* sc = p.slot + (L & (kSlots - 1));
+      LevelSlot* sn = p.slot + ((L + 1) & (kSlots - 1));
+      uint32_t* Ncur = (L & 1) ? p.N1 : p.N0;
+      uint32_t* Noth = (L & 1) ? p.N0 : p.N1;
+      const uint32_t* Vc = vpar ? p.V1 : p.V;
+      uint32_t* Vn = vpar ? p.V : p.V1;
+      if (leader) s_tb = gtimer();
+      auto master_sub = [&](int) {
+        const unsigned long long nf = __ldcg(&sn->n_f), mf = __ldcg(&sn->m_f);
+        s_log[0] = __ldcg(&sc->n_f);
+        s_log[1] = __ldcg(&sc->m_f);
+        s_log[2] = __ldcg(&sc->scanned);
+        s_log[3] = __ldcg(&sc->edges);
+        s_log[4] = __ldcg(&sc->qn);
+        s_tnf = nf;
+        s_unv -= (long long)nf;
+        s_reach_e += mf;
+        s_reach_v += nf;
+        if (nf == 0) return kBitDone;
+        unsigned long long c[6];
+        for (int i = 0; i < 6; ++i) c[i] = __ldcg(&sn->sub[i]);
+        for (int i = 0; i < 3; ++i) s_su[i] -= (long long)c[i];
+        const int dd = sub_rule((sd & 1u) ? 1 : 0, c[0], c[3], s_su[0], s_su[0], p.sf0[0], p.sf1[0]);
+        const int dn = sub_rule((sd & 2u) ? 1 : 0, c[2], c[4], s_su[1], s_su[2], p.sf0[1], p.sf1[1]);
+        const int nd = sub_rule((sd & 4u) ? 1 : 0, c[1], c[5], s_su[2], s_su[1], p.sf0[2], p.sf1[2]);
+        return (dd ? kBitSubDD : 0) | (dn ? kBitSubDN : 0) | (nd ? kBitSubND : 0) | iw_code(s_unv, p);
+      };
+      bool found = false;
+      // normal sources push to normal targets (nn) and, unless nd is backward, to delegates;
+      // delegate sources to delegates unless dd, to normal vertices unless dn is backward
+      const unsigned allow_n = 2u | ((sd & 4u) ? 0u : 1u);
+      const unsigned allow_d = ((sd & 1u) ? 0u : 1u) | ((sd & 2u) ? 0u : 2u);
+      expand_td<true>(p, Vc, L, found, allow_n, allow_d);
+      const unsigned cls_del = ((sd & 1u) ? 1u : 0u) | ((sd & 4u) ? 2u : 0u);
+      const unsigned cls_norm = (sd & 2u) ? 1u : 0u;
+      if (cls_del | cls_norm) expand_bu_sub(p, Vc, L, cls_del, cls_norm, acc, found);
+      flush_block(acc, nullptr, nullptr, &sc->edges, &sc->scanned, nullptr);
+      if (trace) trace_done(sc);
+      const int eb = grid_sync(p, seq, [&](int fl) { return (fl & kFlagFound) ? 0 : master_sub(fl); },
+                               found ? kFlagFound : 0);
+      if (eb < 0) return;
+      if (leader) s_te = gtimer();
+      if (eb & kBitDone) {
+        bits = eb;
+        ended = true;
+      } else {
+        SubAcc sacc;
+        frontier_from_bitmap<true>(p, Vc, Vn, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true,
+                                   true, L + 1, acc, &sacc);
+        flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
+        flush_sub(sacc, sn);
+        if (leader) {
+          p.slot[(L + 2) & (kSlots - 1)] = LevelSlot();
+          p.slot[(L + 2) & (kSlots - 1)].t_first = ~0ull;
+        }
+        bits = grid_sync(p, seq, master_sub);
+      }
+      if (bits < 0) return;
+      if (leader && L < BFS_LOG_LEVELS) {
+        LevelLogDev& lg = p.log[L];
+        lg.t_end = gtimer();
+        lg.dir = sd ? 1 : 0;
+        lg.subdirs = (int)sd;
+        lg.converted = 0;
+        lg.n_f = s_log[0];
+        lg.m_f = s_log[1];
+        lg.scanned = s_log[2];
+        lg.edges = s_log[3];
+        lg.fix_edges = 0ull;
+        lg.found = s_tnf;
+        lg.qn = s_log[4];
+        lg.t_begin = s_tb;
+        lg.t_expand = s_te;
+        lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
+        lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
+      }
+      if (!ended) vpar ^= 1;
+      ++L;
+      continue;
+    }
     const int dir = (bits & kBitBackward) ? 1 : 0;
     const bool conv = (bits & kBitConvert) != 0 && !lists_ready;
     const bool build_lists = dir == 1 && (bits & kBitLists) != 0;
@@ -1086,7 +1489,8 @@ __device__ void run_body(const BfsParams& p) {
       // a backward level with few unvisited vertices left builds the next
       // forward level's lists as it goes, so a switch back needs no conversion
       const int lists = (nd && s_unv * kListsFraction < (long long)p.n_ni) ? kBitLists : 0;
-      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p) | lists;
+      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p) | lists |
+             (nd ? dense_bit(s_unv, p) : 0);
     };
     if (dir == 0 && L == 0 && p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
       first_level(p, src_i, Vn, Ncur, p.Q1, p.CL1, sn, acc);
@@ -1130,7 +1534,7 @@ __device__ void run_body(const BfsParams& p) {
     } else {
       // backward: the items write N, Vn and the cleared other bitmap themselves,
       // so one barrier ends the level unless long rows were deferred
-      const bool deferred = expand_bu(p, Vc, Vn, Noth, L, iw, acc, build_lists);
+      const bool deferred = expand_bu(p, Vc, Vn, Noth, L, iw, acc, build_lists, (bits & kBitDense) != 0);
       flush_block(acc, &sn->n_f, &sn->m_f, &sc->edges, &sc->scanned, nullptr);
       if (trace) trace_done(sc);
       if (leader) {
@@ -1163,6 +1567,7 @@ __device__ void run_body(const BfsParams& p) {
       lg.t_expand = s_te;
       lg.t_first = trace ? __ldcg(&sc->t_first) : 0ull;
       lg.t_last = trace ? __ldcg(&sc->t_last) : 0ull;
+      lg.subdirs = 0;
     }
     lists_ready = build_lists;
     if (!ended) vpar ^= 1;
@@ -1228,6 +1633,42 @@ __device__ void run_body(const BfsParams& p) {
   }
 }
 
+// Delegate neighbours of every non-isolated vertex (one warp per row) and the
+// totals of the per-subgraph schedule's three vertex categories: delegates with
+// a delegate neighbour, normal vertices with a delegate neighbour, delegates
+// with a normal neighbour.
+__global__ void k_deg_del(const int64_t* __restrict__ off, const int32_t* __restrict__ col, int32_t n_ni, int32_t d,
+                          int32_t* __restrict__ deg_del, unsigned long long* __restrict__ tot) {
+  __shared__ unsigned long long s_t[3];
+  if (threadIdx.x < 3) s_t[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = lane_id();
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long t[3] = {0, 0, 0};
+  for (int64_t v = gwarp; v < n_ni; v += nwarps) {
+    const int64_t b = off[v], e = off[v + 1];
+    int c = 0;
+    for (int64_t j = b + lane; j < e; j += 32) c += col[j] < d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+    if (lane == 0) {
+      deg_del[v] = c;
+      const int64_t dn = (e - b) - c;
+      if (v < d) {
+        t[0] += c > 0;
+        t[2] += dn > 0;
+      } else {
+        t[1] += c > 0;
+      }
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    if (t[i]) atomicAdd(&s_t[i], t[i]);
+  __syncthreads();
+  if (threadIdx.x < 3 && s_t[threadIdx.x]) atomicAdd(&tot[threadIdx.x], s_t[threadIdx.x]);
+}
+
 }  // namespace
 
 int configure_run(bfs_graph* g) {
@@ -1247,6 +1688,34 @@ int configure_run(bfs_graph* g) {
   g->variant = variant;
   g->grid_blocks = sms * want;
   if (g->grid_blocks > kMaxBlocks) g->grid_blocks = kMaxBlocks;
+  int per_sm_sub = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_sub, bfs_level_loop<2, kThreads, true>, kThreads, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  if (per_sm_sub < 1) return fail(BFS_ERR_CUDA, "per-subgraph level-loop kernel does not fit on an SM");
+  g->grid_blocks_sub = sms * (per_sm_sub < 2 ? per_sm_sub : 2);
+  if (g->grid_blocks_sub > kMaxBlocks) g->grid_blocks_sub = kMaxBlocks;
+  return BFS_OK;
+}
+
+// The per-subgraph schedule's per-vertex delegate-neighbour counts and category
+// totals, made on its first run (asynchronous on s).
+static int prepare_subgraph(bfs_graph* g, cudaStream_t s) {
+  if (g->deg_del) return BFS_OK;
+  cudaError_t e = cudaMalloc((void**)&g->deg_del, sizeof(int32_t) * ((size_t)g->n_ni + 1));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&g->sub_tot, sizeof(unsigned long long) * 4);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->sub_tot, 0, sizeof(unsigned long long) * 4, s);
+  if (e != cudaSuccess) {
+    if (g->deg_del) cudaFree(g->deg_del);
+    g->deg_del = nullptr;
+    g->sub_tot = nullptr;
+    return cuda_fail(e, "per-subgraph schedule state");
+  }
+  g->device_bytes += (int64_t)sizeof(int32_t) * ((int64_t)g->n_ni + 1) + 32;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (g->n_ni > 0) k_deg_del<<<sms * 4, 256, 0, s>>>(g->off, g->col, g->n_ni, g->d, g->deg_del, g->sub_tot);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "per-subgraph degree pass");
   return BFS_OK;
 }
 
@@ -1259,6 +1728,7 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.internal_of = g->internal_of;
   p.head = g->head;
   p.deg = g->deg;
+  p.lead = g->lead;
   p.longq = g->longq;
   p.V = g->V;
   p.V1 = g->V1;
@@ -1296,6 +1766,17 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.out_vec4 = out_depth8 ? ((((uintptr_t)out_depth8) & 3) == 0 && (((uintptr_t)out_parent) & 15) == 0)
                          : ((((uintptr_t)out_depth) | ((uintptr_t)out_parent)) & 15) == 0;
   p.tuning = g->opt.tuning;
+  const bool sub = g->opt.schedule == BFS_SCHED_PAPER_SUBGRAPH;
+  if (sub) {
+    const int rc = prepare_subgraph(g, s);
+    if (rc) return rc;
+  }
+  p.deg_del = g->deg_del;
+  p.sub_tot = g->sub_tot;
+  for (int i = 0; i < 3; ++i) {
+    p.sf0[i] = g->opt.subgraph_factor0[i];
+    p.sf1[i] = g->opt.subgraph_factor1[i];
+  }
   p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 0) p.epoch = ++g->epoch & 0x0FFFFFFFu;
   if (p.epoch == 1) {  // first run, or the run counter wrapped: barrier words must restart below any tag
@@ -1304,13 +1785,15 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
     if (e0 != cudaSuccess) return cuda_fail(e0, "reset barrier words");
   }
   void* args[] = {&p};
-  const void* fn = g->variant == 3 ? (const void*)bfs_level_loop<3, kThreads>
+  const void* fn = sub                ? (const void*)bfs_level_loop<2, kThreads, true>
+                   : g->variant == 3 ? (const void*)bfs_level_loop<3, kThreads>
                    : g->variant == 1 ? (const void*)bfs_level_loop<1, 2 * kThreads>
                                      : (const void*)bfs_level_loop<2, kThreads>;
   // grid is counted in 512-thread CTAs (the serving slices); a 1024-thread CTA takes two
-  const int want = g->variant == 1 ? (grid + 1) / 2 : grid;
-  const int blocks = want > 0 && want < g->grid_blocks ? want : g->grid_blocks;
-  const int threads = g->variant == 1 ? 2 * kThreads : kThreads;
+  const int want = (!sub && g->variant == 1) ? (grid + 1) / 2 : grid;
+  const int full = sub ? g->grid_blocks_sub : g->grid_blocks;
+  const int blocks = want > 0 && want < full ? want : full;
+  const int threads = (!sub && g->variant == 1) ? 2 * kThreads : kThreads;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
   return BFS_OK;

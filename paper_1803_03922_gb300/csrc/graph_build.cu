@@ -129,10 +129,12 @@ __global__ void k_degree_stats(const int64_t* __restrict__ off, int32_t n_ni, in
 // Per-vertex head record: the first kHead row entries (internal ids, -1 past the
 // end) and their caller ids (with kHead = 4 one 32-byte sector per vertex; with
 // 2 the four ints share one 16-byte word), plus an int32 degree array.  A backward scan that settles within the first entries reads only this
-// sector, indexed by the vertex itself (coalesced across a warp).
+// sector, indexed by the vertex itself (coalesced across a warp).  The lead
+// record is the first entry and its caller id alone (8 bytes): dense backward
+// levels, where the first entry settles most vertices, read only that.
 __global__ void k_heads(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                         const int32_t* __restrict__ caller_of, int32_t n_ni, int4* __restrict__ head,
-                        int32_t* __restrict__ deg) {
+                        int32_t* __restrict__ deg, int2* __restrict__ lead) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_ni; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = off[v], e = off[v + 1];
     int nb[kHead], cid[kHead];
@@ -151,6 +153,7 @@ __global__ void k_heads(const int64_t* __restrict__ off, const int32_t* __restri
       }
     }
     deg[v] = (int32_t)(e - b);
+    lead[v] = make_int2(nb[0], cid[0]);
   }
 }
 
@@ -331,10 +334,11 @@ int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, co
                                               g->d, g->col, sub.as<unsigned long long>());
   BFS_CUDA(cudaMalloc(&g->head, ((size_t)g->n_ni + 1) * kHeadVecs * sizeof(int4)), "alloc head records");
   BFS_CUDA(cudaMalloc(&g->deg, ((size_t)g->n_ni + 4) * 4), "alloc degrees");
-  dev_bytes += ((int64_t)g->n_ni + 1) * kHeadVecs * 16 + ((int64_t)g->n_ni + 4) * 4;
+  BFS_CUDA(cudaMalloc(&g->lead, ((size_t)g->n_ni + 1) * sizeof(int2)), "alloc lead records");
+  dev_bytes += ((int64_t)g->n_ni + 1) * kHeadVecs * 16 + ((int64_t)g->n_ni + 4) * 4 + ((int64_t)g->n_ni + 1) * 8;
   if (g->n_ni > 0) {
     k_degree_stats<<<grid_for(g->n_ni), kB, 0, s>>>(g->off, g->n_ni, g->d, sub.as<unsigned long long>() + 4);
-    k_heads<<<grid_for(g->n_ni), kB, 0, s>>>(g->off, g->col, g->caller_of, g->n_ni, g->head, g->deg);
+    k_heads<<<grid_for(g->n_ni), kB, 0, s>>>(g->off, g->col, g->caller_of, g->n_ni, g->head, g->deg, g->lead);
   }
   BFS_CUDA(cudaGetLastError(), "builder kernels");
   unsigned long long hs[8];
