@@ -109,36 +109,39 @@ def level_list(st):
 def algorithmic_bytes(levels, n, n_ni, d):
     """Bytes one BFS must move, level by level, whatever the kernel does beyond
     them (Sec. IV-A forward visit, Sec. II-C / IV-B backward visit, Sec. VI-A.3
-    output).  Bitmaps span the n_ni non-isolated vertices.
-      forward level:  per frontier vertex its offset pair (8 B) and its row
-                      (4 B per entry), one 4-byte state probe per row entry, and
-                      per newly reached vertex depth, parent, its queue entry
-                      written now and read by the next level (16 B);
-      backward level: one pass over the visited bitmap (n_ni/8 B), per scanned
-                      vertex its offset pair (8 B), per examined entry its column
-                      and the frontier probe (8 B), depth, parent and the
-                      frontier bit of each vertex found (12 B);
+    output); the device computes the same count from the same counters
+    (bfs_stats.model_bytes).  B = one pass over the visited bitmap (4 bytes per
+    32 non-isolated vertices), D = over its delegate prefix.
+      forward level:  per frontier vertex its offset pair (8 B), per row entry
+                      its column and one state probe (8 B), per newly reached
+                      vertex depth, parent and its queue entry written now and
+                      read by the next level (16 B);
+      backward level: one pass over the visited bitmap (B), per scanned vertex
+                      its offset pair (8 B), per examined entry its column and
+                      the frontier probe (8 B), depth, parent and the frontier
+                      bit of each vertex found (12 B);
       level end:      the delegate and the whole bitmap, read and written
-                      (2 (d/8 + n_ni/8) B), and the next level's queue (4 B per
-                      entry) when that level is forward; none after a level that
-                      found nothing;
+                      (2 (D + B)), and the next level's queue (4 B per entry)
+                      when that level is forward; none after a level that found
+                      nothing;
       output:         depth and parent of all n vertices (8n B), once per run.
-    Returns (per-level bytes summed, by phase: forward_expand, forward_level_end,
-    backward_level)."""
-    bm = n_ni / 8.0
-    ph = {"forward_expand": 0.0, "forward_level_end": 0.0, "backward_level": 0.0}
+    Returns (total, per-level bytes by phase: forward_expand,
+    forward_level_end, backward_level)."""
+    B = 4 * ((n_ni + 31) // 32)
+    D = 4 * ((d + 31) // 32)
+    ph = {"forward_expand": 0, "forward_level_end": 0, "backward_level": 0}
     for i, lv in enumerate(levels):
-        end = 0.0
+        end = 0
         if lv["found"] > 0:
-            end = 2.0 * (d / 8.0 + bm)
+            end = 2 * (D + B)
             if i + 1 < len(levels) and levels[i + 1]["dir"] == 0:
-                end += 4.0 * levels[i + 1]["queue"]
+                end += 4 * levels[i + 1]["queue"]
         if lv["dir"] == 0:
-            ph["forward_expand"] += 8.0 * lv["frontier"] + 8.0 * lv["m_f"]
-            ph["forward_level_end"] += 16.0 * lv["found"] + end
+            ph["forward_expand"] += 8 * lv["frontier"] + 8 * lv["m_f"]
+            ph["forward_level_end"] += 16 * lv["found"] + end
         else:
-            ph["backward_level"] += bm + 8.0 * lv["scanned"] + 8.0 * lv["k"] + 12.0 * lv["found"] + end
-    return sum(ph.values()) + 8.0 * n, ph
+            ph["backward_level"] += B + 8 * lv["scanned"] + 8 * lv["k"] + 12 * lv["found"] + end
+    return sum(ph.values()) + 8 * n, ph
 
 
 # ---- clocks during the timed region ---------------------------------------------------------
@@ -267,17 +270,16 @@ class DeviceWorkload:
         self.depth = torch.empty(self.n, dtype=torch.int32, device="cuda")
         self.parent = torch.empty(self.n, dtype=torch.int32, device="cuda")
         # untimed pass: per-source traversal size, byte counts and level log
-        self.ce, self.model, self.alg, self.levels, self.dirs, self.phase = [], [], [], [], [], []
+        self.ce, self.alg, self.levels, self.dirs, self.phase = [], [], [], [], []
         # per phase: [algorithmic bytes, device ns] summed over the sources (level log)
         self.phases = {"forward_expand": [0, 0], "forward_level_end": [0, 0], "backward_level": [0, 0]}
         self.setup_result_ns = 0
         for s in self.sources:
             _, _, st = self.g.run(int(s), self.depth, self.parent, stats=True)
             self.ce.append(st.component_edges)
-            self.model.append(st.model_bytes)
             lvls = level_list(st)
-            alg, by_phase = algorithmic_bytes(lvls, self.n, self.info.n_nonisolated, self.info.delegates)
-            self.alg.append(alg)
+            _, by_phase = algorithmic_bytes(lvls, self.n, self.info.n_nonisolated, self.info.delegates)
+            self.alg.append(st.model_bytes)  # the same count, computed on the device side
             self.levels.append(st.levels)
             self.dirs.append("".join("B" if lv["dir"] else "T" for lv in lvls))
             td = bu = 0
@@ -884,7 +886,6 @@ def main():
         value = hmean(dw.gteps(times))
         run_max = run_s
     k = len(dw.sources)
-    model_total = sum(dw.model[i % k] for i in range(len(times)))
     alg_total = sum(dw.alg[i % k] for i in range(len(times)))
     achieved = alg_total / run_s / 1e9
     peak, peak_kind = measured_peak_hbm()
@@ -901,14 +902,13 @@ def main():
         "data": "synthetic (seeded RMAT, Graph500 parameters)",
         "config": dict(config_of(args.workload, w, dw.info),
                        parallelism="replicas" if ws > 1 else "single GPU"),
-        "gpu_launches": len(times),
+        "gpu_launches": 2 * len(times),  # per BFS: the level loop and the result pass
         "clocks": clocks,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "bfs_level_loop", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": alg_total / len(times),
                      "traffic_over_algorithmic": traffic / (alg_total / len(times)) if traffic else None,
-                     "kernel_model_bytes_per_launch": model_total / len(times),
                      "launch_ms_mean": 1e3 * run_s / len(times)},
         "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * dw.n * k},

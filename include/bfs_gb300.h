@@ -164,9 +164,12 @@ typedef struct bfs_stats {
   int64_t reached;         /* vertices with depth >= 0 */
   int64_t component_edges; /* unique undirected edges in the traversed component (GTEPS numerator) */
   int64_t edges_examined;  /* sum over levels */
-  int64_t model_bytes;     /* algorithmic HBM bytes of this run, from the per-level counters: a
-                              column and a probe per examined entry, offsets and queue entries per
-                              frontier vertex, depth/parent/queue per found vertex, bitmap passes */
+  int64_t model_bytes;     /* algorithmic bytes of this run, from the per-level counters: forward
+                              levels 8 per frontier vertex + 8 per row entry + 16 per vertex found;
+                              backward levels one visited-bitmap pass + 8 per scanned vertex + 8 per
+                              examined entry + 12 per vertex found; every level that found something
+                              a merge of the delegate and whole bitmaps (read and written) and the
+                              next forward level's queue (4 per entry); 8 n of output */
   uint64_t device_ns;      /* %globaltimer span of the whole run (set-up, levels, results) */
   uint64_t setup_ns;       /* part of device_ns spent clearing state before level 0 */
   uint64_t result_ns;      /* part of device_ns spent writing the caller-indexed results */

@@ -83,7 +83,12 @@ int alloc_run_state(bfs_graph* g) {
   if ((rc = dmalloc(&g->V1, words, &t, "alloc V1"))) return rc;
   if ((rc = dmalloc(&g->N0, words, &t, "alloc N"))) return rc;
   if ((rc = dmalloc(&g->N1, words, &t, "alloc N"))) return rc;
-  if ((rc = dmalloc(&g->depth_i, (size_t)g->n_ni + 1, &t, "alloc depth"))) return rc;
+  // depth nibble planes (4 bits per vertex each, a 16-byte word per visited-bitmap
+  // word): enough nibbles for any depth below n_ni
+  g->planes_n = 1;
+  while (g->planes_n < 8 && ((int64_t)1 << (4 * g->planes_n)) <= (int64_t)g->n_ni) ++g->planes_n;
+  g->pstride = (g->words + 1) * 4;
+  if ((rc = dmalloc(&g->planes, (size_t)g->pstride * g->planes_n + 4, &t, "alloc depth planes"))) return rc;
   if ((rc = dmalloc(&g->parent_i, (size_t)g->n_ni + 8, &t, "alloc parent"))) return rc;
   if ((rc = dmalloc(&g->Q0, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
   if ((rc = dmalloc(&g->Q1, (size_t)g->n_ni + 1, &t, "alloc queue"))) return rc;
@@ -104,7 +109,7 @@ int alloc_run_state(bfs_graph* g) {
 }
 
 void free_all(bfs_graph* g) {
-  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->lead, g->V, g->V1, g->N0, g->N1, g->depth_i,
+  void* ptrs[] = {g->off, g->col, g->caller_of, g->internal_of, g->head, g->deg, g->lead, g->V, g->V1, g->N0, g->N1, g->planes, g->crank,
                   g->parent_i, g->Q0, g->Q1, g->CL0, g->CL1, g->longq, g->slot, g->log, g->hdr, g->arrive, g->out_scratch,
                   g->deg_del, g->sub_tot};
   for (void* p : ptrs)
@@ -154,34 +159,32 @@ void* pinned_device_ptr(void* p) {
 }
 
 
-// Algorithmic HBM bytes of one run, from the per-level counters: forward level
-// 20*|F| + 8*m_f + 12*found (+ 16*found + 8*parent_edges with PULL parents);
-// backward level words*4 + 8*scanned +
-// 8*edges + 12*found; every level end 4 bitmap passes, except a level 0 run
-// straight from the source's row (forward, atomicMin parents) and a forward
-// level that found nothing; a conversion one
-// bitmap pass + 4 per queue entry, or only the 4 per entry when the sparse
-// backward level before built the queue; the run's set-up 4 bitmap clears
-// (+ 4*n_ni for atomicMin parents) and the result pass 12*n + 8*reached + words*4.
+// Algorithmic bytes of one run, from its per-level counters: what the method
+// must move level by level (Sec. IV-A forward visit, Sec. II-C / IV-B backward
+// visit, Sec. VI-A.3 output), whatever the kernel moves beyond it.  With B = one
+// pass over the visited bitmap (4 * words) and D = over its delegate prefix:
+//   forward level:  8 per frontier vertex (offset pair), 8 per row entry (the
+//                   column and one state probe), 16 per vertex found (depth,
+//                   parent, queue entry written now and read next level);
+//   backward level: B, 8 per scanned vertex (offset pair), 8 per examined entry
+//                   (column and frontier probe), 12 per vertex found (depth,
+//                   parent, frontier bit);
+//   level end (a level that found something): 2 (D + B) for the bitmap merge,
+//                   and 4 per queue entry of the next level when it is forward;
+//   output: 8 n (depth and parent of every vertex), once.
 int64_t model_bytes_from_log(const bfs_graph* g, const bfs_stats* st) {
-  const int64_t bm = g->words * 4;  // one pass over a bitmap
-  const bool atomicmin = g->opt.td_parent == BFS_TD_PARENT_ATOMICMIN;
-  int64_t b = 4 * bm + 12 * (int64_t)g->n + 8 * st->reached + bm;
-  if (atomicmin) b += 4 * (int64_t)g->n_ni;
+  const int64_t B = g->words * 4, D = ((int64_t)g->d + 31) / 32 * 4;
+  int64_t b = 8 * (int64_t)g->n;
   for (int L = 0; L < st->logged_levels; ++L) {
     const bfs_level_log& l = st->level[L];
-    if (l.converted) b += bm + 4 * l.queue_entries;
-    // a sparse backward level that built this forward level's queue wrote its entries
-    else if (l.direction == 0 && L > 0 && st->level[L - 1].direction == 1) b += 4 * l.queue_entries;
-    if (l.direction == 0) {
-      b += 20 * l.frontier + 8 * l.frontier_edges + 12 * l.found;
-      if (g->opt.td_parent == BFS_TD_PARENT_PULL) b += 16 * l.found + 8 * l.parent_edges;
-    } else {
-      b += bm + 8 * l.scanned + 8 * l.edges_examined + 12 * l.found;
+    if (l.direction == 0)
+      b += 8 * l.frontier + 8 * l.frontier_edges + 16 * l.found;
+    else
+      b += B + 8 * l.scanned + 8 * l.edges_examined + 12 * l.found;
+    if (l.found > 0) {
+      b += 2 * (D + B);
+      if (L + 1 < st->logged_levels && st->level[L + 1].direction == 0) b += 4 * st->level[L + 1].queue_entries;
     }
-    // no level-end sweeps after level 0 from the source's row, nor after a
-    // forward level that found nothing (the run ends at its first barrier)
-    if (!(L == 0 && l.direction == 0 && atomicmin) && !(l.direction == 0 && l.found == 0)) b += 4 * bm;
   }
   return b;
 }

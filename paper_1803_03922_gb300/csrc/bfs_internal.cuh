@@ -79,7 +79,8 @@ struct BfsParams {
   uint32_t* V1;              // the other (depth <= L and depth <= L+1)
   uint32_t* N0;              // discovered-this-level bitmaps, [words] each
   uint32_t* N1;
-  int32_t* depth_i;          // [n_ni]
+  uint32_t* planes;          // depth nibble planes: plane k (< planes_n) at planes + k * pstride,
+                             // 8 vertices per word (4 words per visited-bitmap word)
   int32_t* parent_i;         // [n_ni], caller ids
   int32_t* longq;            // vertices whose backward scan is deferred to the end of the level, [long_cap]
   int32_t* Q0;               // normal-vertex frontier queues, [n_ni] each
@@ -93,8 +94,12 @@ struct BfsParams {
   int32_t* out_depth;        // [n] caller-indexed (unused when out_depth8 is set)
   int32_t* out_parent;       // [n] or null
   uint8_t* out_depth8;       // [n] uint8 depth (255 unreached) instead of out_depth, or null
+  const int4* crank;         // [ceil(n/32)] per caller word: delegate bits, non-isolated normal bits,
+                             // delegates and non-isolated normal vertices before the word
   int64_t nnz;
   int64_t words;             // ceil(n_ni / 32)
+  int64_t pstride;           // words of a nibble plane: 4 (words + 1), a multiple of 4
+  int32_t planes_n;          // nibble planes: enough for any depth below n_ni
   int32_t n, n_ni, d;
   int32_t src_c;             // source, caller id
   int32_t schedule;
@@ -139,7 +144,10 @@ struct bfs_graph {
   uint32_t* V1 = nullptr;
   uint32_t* N0 = nullptr;
   uint32_t* N1 = nullptr;
-  int32_t* depth_i = nullptr;
+  uint32_t* planes = nullptr;      // depth nibble planes
+  int32_t planes_n = 0;
+  int64_t pstride = 0;
+  int4* crank = nullptr;           // caller-rank words (built with the graph)
   int32_t* parent_i = nullptr;
   int32_t* Q0 = nullptr;
   int32_t* Q1 = nullptr;

@@ -54,6 +54,71 @@ __device__ void flush_block(Acc& a, unsigned long long* nf, unsigned long long* 
   a = Acc();
 }
 
+// Depth is kept as 4-bit nibbles, eight vertices per 32-bit word (nibble
+// plane k holds bits 4k..4k+3 of every vertex's depth; plane 0 alone covers
+// depths below 16).  The owner of a visited-bitmap word w writes the nibbles of
+// the word's vertices f found at depth D as one 16-byte store or OR, instead of
+// a 4-byte store per vertex, and the result pass reads one word per 8 vertices.
+// Plane 0 is cleared by the run's set-up; plane k >= 1 is first needed at
+// D = 16^k, and that level's word owners store there, clearing what an earlier
+// run left.  A vertex's depth is nonzero unless it is the source or unreached.
+
+// The 32 bits of f spread to 32 nibbles (four words of eight), each nibble = x
+// (0..15) where its bit is set.
+__device__ __forceinline__ uint4 spread_nibbles(unsigned f, unsigned x) {
+  unsigned q[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned b = (f >> (8 * i)) & 0xFFu;
+    b = (b | (b << 12)) & 0x000F000Fu;
+    b = (b | (b << 6)) & 0x03030303u;
+    b = (b | (b << 3)) & 0x11111111u;
+    q[i] = b * x;
+  }
+  return make_uint4(q[0], q[1], q[2], q[3]);
+}
+
+// Called once per word by the level's owner of visited-bitmap word w (an
+// all-word pass) with the word's vertices f found at depth D.
+__device__ __forceinline__ void plane_store(const BfsParams& p, int64_t w, unsigned f, int D) {
+  uint4* p0 = reinterpret_cast<uint4*>(p.planes) + w;
+  if (f && (D & 15)) {
+    const uint4 a = spread_nibbles(f, (unsigned)(D & 15));
+    uint4 o = *p0;
+    o.x |= a.x;
+    o.y |= a.y;
+    o.z |= a.z;
+    o.w |= a.w;
+    *p0 = o;
+  }
+  if (D >= 16) {
+    for (int k = 1; k < p.planes_n; ++k) {
+      const unsigned x = (unsigned)(D >> (4 * k)) & 15u;
+      uint4* pk = reinterpret_cast<uint4*>(p.planes + (int64_t)k * p.pstride) + w;
+      if (D == (1 << (4 * k))) {
+        *pk = spread_nibbles(f, x);
+      } else if (f && x) {
+        const uint4 a = spread_nibbles(f, x);
+        uint4 o = *pk;
+        o.x |= a.x;
+        o.y |= a.y;
+        o.z |= a.z;
+        o.w |= a.w;
+        *pk = o;
+      }
+    }
+  }
+}
+
+// Depth nibbles of one vertex found at depth D outside an all-word pass (level 0
+// from the source's row, deferred long rows): atomics, after the owners' stores.
+__device__ __forceinline__ void plane_or(const BfsParams& p, int v, int D) {
+  for (int k = 0; k < p.planes_n && (D >> (4 * k)); ++k) {
+    const unsigned x = (unsigned)(D >> (4 * k)) & 15u;
+    if (x) atomicOr(p.planes + (int64_t)k * p.pstride + (v >> 3), x << (4 * (v & 7)));
+  }
+}
+
 // Visited-state probe for the pull scans, against the level's visited bitmap Vc
 // (vertices at depth <= L; read-only during level L, whose discoveries go to the
 // other buffer).  For an unvisited vertex (backward) or one found in level L
@@ -616,7 +681,6 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
       acc.edges += (unsigned long long)(q ? kB : kA);
       if (hit >= 0) {
         p.parent_i[v] = q ? cidB : cidA;
-        p.depth_i[v] = L + 1;
         acc.nf += 1;
         acc.mf += (unsigned long long)(q ? hB.deg : hA.deg);
       }
@@ -633,6 +697,7 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
     Vn[w] = vraw | f;
     Nclr[w] = 0u;
     found[lane] = 0u;
+    plane_store(p, w, f, L + 1);
   }
   if (qslot) append_next(p, w * 32, f, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, qslot);
   __syncwarp();
@@ -666,7 +731,6 @@ __device__ bool bu_settle(const BfsParams& p, const uint32_t* __restrict__ Vc, i
       acc.edges += (unsigned long long)k;
       if (hit >= 0) {
         p.parent_i[v] = cid;
-        p.depth_i[v] = L + 1;
         acc.nf += 1;
         acc.mf += (unsigned long long)h.deg;
         atomicOr(found + ((v >> 5) - w0), 1u << (v & 31));
@@ -723,7 +787,6 @@ __device__ bool bu_dense_item(const BfsParams& p, const uint32_t* __restrict__ V
       const bool more = un[u] && !h0 && dg[u] > 1;
       if (h0) {
         p.parent_i[v] = a[u].y;
-        p.depth_i[v] = L + 1;
         acc.nf += 1;
         acc.mf += (unsigned long long)dg[u];
       }
@@ -763,6 +826,7 @@ __device__ bool bu_dense_item(const BfsParams& p, const uint32_t* __restrict__ V
     N[wl] = f;
     Vn[wl] = vraw | f;
     Nclr[wl] = 0u;
+    plane_store(p, wl, f, L + 1);
   }
   found[lane] = 0u;
   if (qslot) append_next(p, wl * 32, f, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, qslot);
@@ -897,7 +961,7 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
       acc.edges += (unsigned long long)kv;
       if (hit >= 0) {
         p.parent_i[v] = p.caller_of[hit];
-        p.depth_i[v] = L + 1;
+        plane_or(p, v, L + 1);
         atomicOr(Ncur + (v >> 5), 1u << (v & 31));
         atomicOr(Vn + (v >> 5), 1u << (v & 31));
         acc.nf += 1;
@@ -989,6 +1053,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
         Vn[w] = Vc[w] | nb;
         Nclr[w] = 0u;
       }
+      if (count) plane_store(p, w, nb, depth);
     }
     if (!__any_sync(kFull, nb != 0)) continue;
     const int64_t v0 = w * 32;
@@ -1027,7 +1092,6 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
       unsigned long long nc = 0;
       if (act) {
         if (count) {
-          p.depth_i[v] = depth;
           acc.nf += 1;
           acc.mf += (unsigned long long)dg;
           if constexpr (kSub) sub_count(p, v, dg, *sacc);
@@ -1085,7 +1149,7 @@ __device__ void first_level(const BfsParams& p, int s, uint32_t* __restrict__ Vn
     const int u = act ? p.col[e] : 0;
     const int dg = act ? p.deg[u] : 0;
     if (act) {
-      p.depth_i[u] = 1;
+      plane_or(p, u, 1);
       p.parent_i[u] = p.src_c;
       atomicOr(N + (u >> 5), 1u << (u & 31));
       atomicOr(Vn + (u >> 5), 1u << (u & 31));
@@ -1291,6 +1355,8 @@ __device__ void run_body(const BfsParams& p) {
     reinterpret_cast<uint4*>(p.N0)[q] = make_uint4(0, 0, 0, 0);
     reinterpret_cast<uint4*>(p.N1)[q] = make_uint4(0, 0, 0, 0);
   }
+  // depth nibble plane 0: one 16-byte word per visited-bitmap word
+  for (int64_t q = gtid; q < p.words; q += gthreads) reinterpret_cast<uint4*>(p.planes)[q] = make_uint4(0, 0, 0, 0);
   if (kSub || p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
     const int64_t P4 = ((int64_t)p.n_ni + 3) / 4;
     for (int64_t q = gtid; q < P4; q += gthreads) {
@@ -1314,7 +1380,6 @@ __device__ void run_body(const BfsParams& p) {
     }
     p.hdr->t0 = gtimer();
     if (src_in) {
-      p.depth_i[src_i] = 0;
       p.parent_i[src_i] = p.src_c;
       p.slot[0].n_f = 1;
       p.slot[0].m_f = src_deg;
@@ -1574,60 +1639,12 @@ __device__ void run_body(const BfsParams& p) {
     ++L;
   }
 
-  // ---- results in caller ids: 4 consecutive caller ids per thread ----
+  // ---- the results in caller ids are written by bfs_results, launched next ----
   if (leader) p.hdr->t_loop = gtimer();
-  const uint32_t* Vf = vpar ? p.V1 : p.V;
-  const int64_t C4 = ((int64_t)p.n + 3) / 4;
-  for (int64_t q = gtid; q < C4; q += gthreads) {
-    const int4 iv = reinterpret_cast<const int4*>(p.internal_of)[q];
-    const int vs[4] = {iv.x, iv.y, iv.z, iv.w};
-    int dv[4], pv[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int v = vs[t];
-      const bool r = v >= 0 && v < p.n_ni && ((Vf[v >> 5] >> (v & 31)) & 1u);
-      dv[t] = r ? p.depth_i[v] : -1;
-      pv[t] = r ? p.parent_i[v] : -1;
-      if (q * 4 + t == p.src_c) {
-        dv[t] = 0;
-        pv[t] = p.src_c;
-      }
-    }
-    const int64_t c = q * 4;
-    if (p.out_depth8) {  // uint8 form: 255 = unreached
-      unsigned d8 = 0;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (dv[t] > 254) set_failed(p, BFS_ERR_OVERFLOW);
-        d8 |= (unsigned)(dv[t] < 0 ? 255 : (dv[t] & 0xFF)) << (8 * t);
-      }
-      if (p.out_vec4 && c + 3 < p.n) {
-        reinterpret_cast<unsigned*>(p.out_depth8)[q] = d8;
-        if (p.out_parent) reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
-      } else {
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (c + t < p.n) {
-            p.out_depth8[c + t] = (uint8_t)(d8 >> (8 * t));
-            if (p.out_parent) p.out_parent[c + t] = pv[t];
-          }
-      }
-    } else if (p.out_vec4 && c + 3 < p.n) {
-      reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
-      reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (c + t < p.n) {
-          p.out_depth[c + t] = dv[t];
-          p.out_parent[c + t] = pv[t];
-        }
-    }
-  }
   if (leader) {
     p.hdr->levels = src_in ? L : 1;
     p.hdr->levels_run = L;
-    p.hdr->t1 = gtimer();
+    p.hdr->t1 = p.hdr->t_loop;
     p.hdr->reached_edges = src_in ? s_reach_e : 0;
     p.hdr->reached = src_in ? s_reach_v : 1;
   }
@@ -1667,6 +1684,98 @@ __global__ void k_deg_del(const int64_t* __restrict__ off, const int32_t* __rest
     if (t[i]) atomicAdd(&s_t[i], t[i]);
   __syncthreads();
   if (threadIdx.x < 3 && s_t[threadIdx.x]) atomicAdd(&tot[threadIdx.x], s_t[threadIdx.x]);
+}
+
+// Results in caller ids, 4 consecutive caller ids per thread: a kernel of its
+// own, launched after the level loop on the same stream (L = levels run).
+
+__global__ void __launch_bounds__(kThreads) bfs_results(BfsParams p) {
+  if (run_failed(p)) return;  // outputs are unspecified after a failed run
+  const int L = *(volatile int*)&p.hdr->levels_run;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  // A caller id's internal id comes from its word of the caller-rank table
+  // (which of the word's callers are delegates / non-isolated normal vertices,
+  // and how many of each precede the word: both classes are numbered in caller
+  // order); isolated vertices are never reached but the source.  The depth is
+  // the vertex's nibbles; zero means unreached (the source is set apart).
+  // nibble planes that hold a depth of this run: the last level run found
+  // nothing, so the deepest vertex is at depth L - 1
+  int nib_used = 1;
+  while (nib_used < p.planes_n && ((L - 1) >> (4 * nib_used)) > 0) ++nib_used;
+  const int64_t C4 = ((int64_t)p.n + 3) / 4;
+  for (int64_t q = gtid; q < C4; q += gthreads) {
+    const int4 rk = p.crank[q >> 3];
+    const int b0 = (int)((q & 7) * 4);
+    int vs[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int b = b0 + t;
+      const unsigned lo = (1u << b) - 1u;
+      int v = -1;
+      if (((unsigned)rk.x >> b) & 1u)
+        v = rk.z + __popc((unsigned)rk.x & lo);
+      else if (((unsigned)rk.y >> b) & 1u)
+        v = p.d + rk.w + __popc((unsigned)rk.y & lo);
+      vs[t] = v;
+    }
+    // the depth word and the parent slot of every non-isolated vertex are loaded
+    // together (almost all of them are reached), so a quad costs two round trips
+    unsigned nw[4];
+    int pp[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      nw[t] = vs[t] >= 0 ? p.planes[vs[t] >> 3] : 0u;
+      pp[t] = vs[t] >= 0 ? p.parent_i[vs[t]] : -1;
+    }
+    int dv[4], pv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int v = vs[t];
+      int dd = v >= 0 ? (int)((nw[t] >> (4 * (v & 7))) & 15u) : 0;
+      for (int k = 1; k < nib_used && v >= 0; ++k)
+        dd |= (int)((p.planes[(int64_t)k * p.pstride + (v >> 3)] >> (4 * (v & 7))) & 15u) << (4 * k);
+      const bool r = dd > 0;
+      dv[t] = r ? dd : -1;
+      pv[t] = r ? pp[t] : -1;
+      if (q * 4 + t == p.src_c) {
+        dv[t] = 0;
+        pv[t] = p.src_c;
+      }
+    }
+    const int64_t c = q * 4;
+    if (p.out_depth8) {  // uint8 form: 255 = unreached
+      unsigned d8 = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (dv[t] > 254) set_failed(p, BFS_ERR_OVERFLOW);
+        d8 |= (unsigned)(dv[t] < 0 ? 255 : (dv[t] & 0xFF)) << (8 * t);
+      }
+      if (p.out_vec4 && c + 3 < p.n) {
+        reinterpret_cast<unsigned*>(p.out_depth8)[q] = d8;
+        if (p.out_parent) reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (c + t < p.n) {
+            p.out_depth8[c + t] = (uint8_t)(d8 >> (8 * t));
+            if (p.out_parent) p.out_parent[c + t] = pv[t];
+          }
+      }
+    } else if (p.out_vec4 && c + 3 < p.n) {
+      reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
+      reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c + t < p.n) {
+          p.out_depth[c + t] = dv[t];
+          p.out_parent[c + t] = pv[t];
+        }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) atomicMax(&p.hdr->t1, gtimer());
 }
 
 }  // namespace
@@ -1734,7 +1843,10 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.V1 = g->V1;
   p.N0 = g->N0;
   p.N1 = g->N1;
-  p.depth_i = g->depth_i;
+  p.planes = g->planes;
+  p.planes_n = g->planes_n;
+  p.pstride = g->pstride;
+  p.crank = g->crank;
   p.parent_i = g->parent_i;
   p.Q0 = g->Q0;
   p.Q1 = g->Q1;
@@ -1796,6 +1908,11 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   const int threads = (!sub && g->variant == 1) ? 2 * kThreads : kThreads;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
+  // the results, on the same CTAs' worth of the device (a serving slice stays a slice)
+  const int rblocks = blocks * threads / kThreads;
+  bfs_results<<<rblocks, kThreads, 0, s>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "result-pass launch");
   return BFS_OK;
 }
 

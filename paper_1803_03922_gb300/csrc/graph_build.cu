@@ -87,6 +87,26 @@ __global__ void k_internal_ids(const int32_t* __restrict__ fdel, const int32_t* 
   }
 }
 
+// Caller-rank words: for caller ids [32w, 32w+32), which are delegates and which
+// non-isolated normal vertices, and how many of each precede 32w.  Both classes
+// are numbered in caller order, so a caller id's internal id is its class base
+// plus its rank: the level loop's result pass reads 16 bytes per 32 caller ids
+// instead of internal_of.
+__global__ void k_caller_rank(const int32_t* __restrict__ fdel, const int32_t* __restrict__ fnor,
+                              const int32_t* __restrict__ sdel, const int32_t* __restrict__ snor, int32_t n,
+                              int4* __restrict__ crank) {
+  const int64_t nw = ((int64_t)n + 31) / 32;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+    unsigned md = 0, mn = 0;
+    const int64_t c0 = w * 32;
+    for (int b = 0; b < 32 && c0 + b < n; ++b) {
+      md |= (unsigned)(fdel[c0 + b] != 0) << b;
+      mn |= (unsigned)(fnor[c0 + b] != 0) << b;
+    }
+    crank[w] = make_int4((int)md, (int)mn, sdel[c0], snor[c0]);
+  }
+}
+
 // Column scatter: entry i of caller row u lands at off[internal(u)] + (i - start_c[u])
 // and stores internal(v); rows stay in ascending caller id of the neighbour.
 // Also counts the nn/nd/dn/dd entries (Sec. IV) with the class of each endpoint.
@@ -315,6 +335,10 @@ int build_graph(const int32_t* src, const int32_t* dst, int64_t m, int32_t n, co
   k_internal_ids<<<grid_for(n), kB, 0, s>>>(fdel.as<int32_t>(), fnor.as<int32_t>(), sdel.as<int32_t>(),
                                             snor.as<int32_t>(), start_c.as<int64_t>(), end_c.as<int64_t>(), n, g->d,
                                             g->n_ni, g->internal_of, g->caller_of, deg_int.as<int64_t>());
+  BFS_CUDA(cudaMalloc(&g->crank, (((size_t)n + 31) / 32 + 1) * sizeof(int4)), "alloc caller ranks");
+  dev_bytes += (((int64_t)n + 31) / 32 + 1) * 16;
+  k_caller_rank<<<grid_for(((int64_t)n + 31) / 32), kB, 0, s>>>(fdel.as<int32_t>(), fnor.as<int32_t>(), sdel.as<int32_t>(),
+                                                               snor.as<int32_t>(), n, g->crank);
   {
     size_t t1 = 0;
     BFS_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, t1, deg_int.as<int64_t>(), g->off, (int64_t)g->n_ni + 1, s),

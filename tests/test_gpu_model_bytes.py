@@ -1,11 +1,13 @@
-"""The byte model behind the roofline's achieved bandwidth: the device's
-model_bytes of a run equals the model computed here from the oracle's per-level
-counters (frontier size and degree sum, found, scanned, entries examined, queue
-entries) for the directions the device took, so the bytes the bench divides by
-time are the algorithm's, not a count the kernel could drift from."""
+"""The algorithmic byte count behind the roofline: the device's model_bytes of
+a run equals the count computed here from the oracle's per-level counters
+(frontier size and degree sum, found, scanned, entries examined, queue entries)
+for the directions the device took, so the bytes the bench divides by time are
+the method's, not a count the kernel could drift from.  bench.py's per-phase
+split of the same count must add up to it."""
 import numpy as np
 import pytest
 
+import bench
 import graphgen
 import oracle
 from tests.gpu_util import gpu_bfs, gpu_graph, need_cuda
@@ -15,26 +17,23 @@ pytestmark = pytest.mark.gpu
 
 def _model(og, g, s, st, th):
     info = g.info
-    bm = 4 * ((info.n_nonisolated + 31) // 32)  # one pass over a bitmap
+    B = 4 * ((info.n_nonisolated + 31) // 32)  # one pass over the visited bitmap
+    D = 4 * ((info.delegates + 31) // 32)      # over its delegate prefix
     want_d, _ = og.bfs(s)
     L = st.logged_levels
     dirs = np.array([st.level[i].direction for i in range(L)], dtype=np.int32)
     cnt = og.level_counters(s, want_d, th, dirs)
-    reached = int((want_d >= 0).sum())
-    b = 4 * bm + 12 * info.n + 8 * reached + bm + 4 * info.n_nonisolated  # set-up, results, parent fill
+    b = 8 * info.n  # depth and parent of every vertex
     for i in range(L):
         frontier, mf, found, scanned, edges, _, queue = (int(x) for x in cnt[i])
-        fwd = dirs[i] == 0
-        if st.level[i].converted:
-            b += bm + 4 * queue
-        elif fwd and i > 0 and dirs[i - 1] == 1:
-            b += 4 * queue  # built by the sparse backward level before
-        if fwd:
-            b += 20 * frontier + 8 * mf + 12 * found
+        if dirs[i] == 0:
+            b += 8 * frontier + 8 * mf + 16 * found
         else:
-            b += bm + 8 * scanned + 8 * edges + 12 * found
-        if not (fwd and i == 0) and not (fwd and found == 0):
-            b += 4 * bm  # level-end bitmap passes
+            b += B + 8 * scanned + 8 * edges + 12 * found
+        if found > 0:
+            b += 2 * (D + B)
+            if i + 1 < L and dirs[i + 1] == 0:
+                b += 4 * int(cnt[i + 1][6])
     return b
 
 
@@ -51,4 +50,7 @@ def test_model_bytes_from_oracle_counters(sched):
     for s in graphgen.sample_sources(mask, 6, seed=16161):
         _, _, st = gpu_bfs(g, int(s), stats=True)
         assert st.model_bytes == _model(og, g, int(s), st, th), "source %d" % s
+        info = g.info
+        total, phases = bench.algorithmic_bytes(bench.level_list(st), info.n, info.n_nonisolated, info.delegates)
+        assert total == st.model_bytes and sum(phases.values()) + 8 * info.n == total
     g.close()

@@ -331,3 +331,23 @@ def test_first_level_from_source_row(th):
         for tdp in (0, 1):
             g.set_options(td_parent=tdp, **opts)
             check_against_oracle(og, g, [0, 7, n_leaf, n_leaf + 1, n_leaf + 4], stats=True, th=th)
+
+
+@pytest.mark.parametrize("sched", ["beamer", "topdown", "bottomup", "alternate"])
+def test_deep_paths_all_depth_nibbles(sched):
+    """Depths well past 15, 255 and 4095 (the depth is kept in 4-bit nibbles, a
+    plane of them per 4 bits): a path of 4200 vertices with a pendant star and a
+    ragged vertex count, from an end, from the middle and from a star leaf;
+    then a short run on the same graph, so that nibbles a deep run left behind
+    must not leak into the next result."""
+    n = 4200 + 45
+    e = [(i, i + 1) for i in range(4199)] + [(4199, 4200 + k) for k in range(45)]
+    e = np.asarray(e, dtype=np.int32)
+    og = oracle.Graph(n, e[:, 0], e[:, 1])
+    g = gpu_graph(n, e[:, 0], e[:, 1], th=8, **SCHEDULES[sched])
+    for s in (0, 2100, 4230, 4199):
+        want_d, want_p = og.bfs(s)
+        d, p = gpu_bfs(g, s)
+        assert_same(d, want_d, "depth (source %d)" % s)
+        assert_same(p, want_p, "parent (source %d)" % s)
+    g.close()
