@@ -40,6 +40,8 @@ struct CUstream_st; /* cudaStream_t is `struct CUstream_st*` */
 #define BFS_ERR_OVERFLOW (-3) /* a size beyond the int32/int64 layout, or a batched depth > 254 */
 #define BFS_ERR_TIMEOUT (-4)  /* a bounded device-side wait expired; the context stays usable */
 #define BFS_ERR_CUDA (-5)     /* a CUDA runtime call failed */
+#define BFS_ERR_CHECK (-6)    /* a bounds check of a library built with BFS_CHECK failed: an index of a
+                                 kernel fell outside its array; the access was skipped (no trap) */
 
 /* Direction schedules.  The output never depends on the schedule (Sec. IV-B:
  * a visit direction changes only the work, not the input or the output). */
@@ -215,8 +217,8 @@ typedef struct bfs_batch bfs_batch;
 #define BFS_BATCH_LOG_LEVELS 64
 
 typedef struct bfs_batch_level {
-  int32_t direction;          /* 0 forward, 1 backward */
-  int32_t pad;
+  int32_t direction;          /* 1 if any query's lane pulls (backward) at this level, else 0 */
+  int32_t pulled_lanes;       /* lanes that pull; the other lanes with a frontier push (forward) */
   int64_t frontier_vertices;  /* vertices in the union of the queries' frontiers */
   int64_t frontier_edges;     /* their degree sum */
   int64_t pairs;              /* (query, vertex) pairs in the frontier */

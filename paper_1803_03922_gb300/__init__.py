@@ -26,6 +26,7 @@ BFS_ERR_OOM = -2
 BFS_ERR_OVERFLOW = -3
 BFS_ERR_TIMEOUT = -4
 BFS_ERR_CUDA = -5
+BFS_ERR_CHECK = -6
 
 BFS_SCHED_BEAMER = 0
 BFS_SCHED_TOPDOWN = 1
@@ -76,7 +77,7 @@ BFS_BATCH_LOG_LEVELS = 64
 
 
 class bfs_batch_level(ctypes.Structure):
-    _fields_ = [("direction", c_i32), ("pad", c_i32), ("frontier_vertices", c_i64), ("frontier_edges", c_i64),
+    _fields_ = [("direction", c_i32), ("pulled_lanes", c_i32), ("frontier_vertices", c_i64), ("frontier_edges", c_i64),
                 ("pairs", c_i64), ("t_begin_ns", c_u64), ("t_expand_ns", c_u64), ("t_end_ns", c_u64)]
 
 
@@ -116,13 +117,15 @@ _lib = None
 
 
 def _load():
+    """The CUDA library: libbfs_gb300.so, or the build named by the environment
+    variable BFS_GB300_LIB (the bounds-checked build, libbfs_gb300_check.so)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = os.environ.get("BFS_GB300_LIB") or _build.LIB
     if not os.path.exists(path):
-        raise ImportError("libbfs_gb300.so is not built; run __graft_entry__.build() "
-                          "(the CUDA library is the only implementation)")
+        raise ImportError("%s is not built; run __graft_entry__.build() "
+                          "(the CUDA library is the only implementation)" % os.path.basename(path))
     lib = ctypes.CDLL(path)
     lib.bfs_options_default.argtypes = [ctypes.POINTER(bfs_options)]
     lib.bfs_build_graph.argtypes = [c_vp, c_vp, c_i64, c_i32, ctypes.POINTER(bfs_options),

@@ -140,6 +140,7 @@ int run_status(bfs_graph* g, RunHeader* h) {
   if (h->err != 0 && (h->err >> 4) == (g->epoch & 0x0FFFFFFFu)) {
     int code = -(int)(h->err & 0xFu);
     if (code == BFS_ERR_TIMEOUT) return fail(code, "a device-side grid barrier wait passed its deadline");
+    if (code == BFS_ERR_CHECK) return fail(code, "a bounds check of the BFS_CHECK build failed in the level loop");
     return fail(code, "the level-loop kernel reported an error");
   }
   return BFS_OK;

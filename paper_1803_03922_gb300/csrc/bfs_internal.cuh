@@ -99,6 +99,7 @@ struct BfsParams {
   int64_t nnz;
   int64_t words;             // ceil(n_ni / 32)
   int64_t pstride;           // words of a nibble plane: 4 (words + 1), a multiple of 4
+  int64_t cl_cap, long_cap;  // entries of the chunk lists and of the long-row list
   int32_t planes_n;          // nibble planes: enough for any depth below n_ni
   int32_t n, n_ni, d;
   int32_t src_c;             // source, caller id

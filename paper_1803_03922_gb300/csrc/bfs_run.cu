@@ -81,6 +81,7 @@ __device__ __forceinline__ uint4 spread_nibbles(unsigned f, unsigned x) {
 // Called once per word by the level's owner of visited-bitmap word w (an
 // all-word pass) with the word's vertices f found at depth D.
 __device__ __forceinline__ void plane_store(const BfsParams& p, int64_t w, unsigned f, int D) {
+  if (!BFS_IN(p, w, p.words)) return;
   uint4* p0 = reinterpret_cast<uint4*>(p.planes) + w;
   if (f && (D & 15)) {
     const uint4 a = spread_nibbles(f, (unsigned)(D & 15));
@@ -113,6 +114,7 @@ __device__ __forceinline__ void plane_store(const BfsParams& p, int64_t w, unsig
 // Depth nibbles of one vertex found at depth D outside an all-word pass (level 0
 // from the source's row, deferred long rows): atomics, after the owners' stores.
 __device__ __forceinline__ void plane_or(const BfsParams& p, int v, int D) {
+  if (!BFS_IN(p, v, p.n_ni)) return;
   for (int k = 0; k < p.planes_n && (D >> (4 * k)); ++k) {
     const unsigned x = (unsigned)(D >> (4 * k)) & 15u;
     if (x) atomicOr(p.planes + (int64_t)k * p.pstride + (v >> 3), x << (4 * (v & 7)));
@@ -130,6 +132,7 @@ __device__ __forceinline__ bool probe(const BfsParams& p, int c, const uint32_t*
   if constexpr (kSub) {
     if (!((c < p.d) ? (cls & 1u) : (cls & 2u))) return false;
   }
+  if (!BFS_IN(p, c, p.n_ni)) return false;
   return (Vc[c >> 5] >> (c & 31)) & 1u;
 }
 
@@ -144,7 +147,7 @@ __device__ int warp_scan(const BfsParams& p, int64_t rbeg, int64_t from, int64_t
     const int64_t j = j0 + lane * 4;
     unsigned best = 0xFFFFFFFFu;
     int bc = -1;
-    if (j < end) {
+    if (j < end && BFS_IN(p, j + 3, p.nnz + kColPad)) {
       const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.col + j));
       const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
@@ -211,7 +214,7 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
     while (__any_sync(kFull, !gdone)) {
       const int64_t j = pos + sub * P;
       int c = -1, t0 = 0;  // this lane's first passing entry and its offset in the lane's P entries
-      if (!gdone && j < rend) {
+      if (!gdone && j < rend && BFS_IN(p, j + P - 1, p.nnz + kColPad)) {
         if constexpr (P == 1) {
           const int c1 = p.col[j];
           if (probe<kFix, kSub>(p, c1, Ncur, gcls)) c = c1;
@@ -275,7 +278,8 @@ __device__ void pull_rest(const BfsParams& p, bool more, int64_t beg, int64_t en
     if (lane == 0) base = atomicAdd(&defer_slot->nlong, (unsigned long long)__popc(lrem));
     base = __shfl_sync(kFull, base, 0);
     if (longrow) {
-      p.longq[base + __popc(lrem & ((1u << lane) - 1u))] = defer_v;
+      const unsigned long long at = base + __popc(lrem & ((1u << lane) - 1u));
+      if (BFS_IN(p, at, p.long_cap)) p.longq[at] = defer_v;
       hit = kDeferred;
     }
     lrem = 0;
@@ -309,7 +313,7 @@ __device__ __forceinline__ HeadRec head_load(const BfsParams& p, bool act, int v
 #pragma unroll
   for (int t = 0; t < kHead; ++t) h.nb[t] = h.cid[t] = -1;
   h.deg = 0;
-  if (act) {
+  if (act && BFS_IN(p, v, p.n_ni)) {
     if constexpr (kHead >= 4) {
 #pragma unroll
       for (int t = 0; t < kHead; t += 4) {
@@ -401,7 +405,7 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
                                          int pcaller, uint32_t* __restrict__ N, bool& found, unsigned allow = 3u) {
   unsigned vw[4];
 #pragma unroll
-  for (int t = 0; t < 4; ++t) vw[t] = v[t] >= 0 ? Vc[(unsigned)v[t] >> 5] : kFull;
+  for (int t = 0; t < 4; ++t) vw[t] = (v[t] >= 0 && BFS_IN(p, v[t], p.n_ni)) ? Vc[(unsigned)v[t] >> 5] : kFull;
   // consecutive row entries often fall in one bitmap word (delegates are numbered in
   // caller order, and rows are sorted by caller id): their discovered bits are
   // OR-ed together and set with one atomic per run of equal words
@@ -435,7 +439,7 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
   int64_t beg = 0, deg = 0;
-  if (u >= 0) {
+  if (u >= 0 && BFS_IN(p, u, p.n_ni)) {
     beg = p.off[u];
     deg = p.deg[u];
   }
@@ -453,7 +457,8 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
     const int64_t ob = __shfl_sync(kFull, beg, pos);
     const int64_t ox = __shfl_sync(kFull, excl, pos);
     const int ou = __shfl_sync(kFull, u, pos);
-    int v = e < total ? p.col[ob + (e - ox)] : -1;
+    int v = (e < total && BFS_IN(p, ob + (e - ox), p.nnz)) ? p.col[ob + (e - ox)] : -1;
+    if (v >= 0 && !BFS_IN(p, v, p.n_ni)) v = -1;
     if constexpr (kSub) {  // per-subgraph directions: only targets of the classes in allow
       if (v >= 0 && !((v < p.d) ? (allow & 1u) : (allow & 2u))) v = -1;
     }
@@ -475,6 +480,7 @@ __device__ void td_chunk(const BfsParams& p, const uint32_t* __restrict__ Vc, in
                          bool& found, unsigned allow = 3u) {
   const int lane = lane_id();
   const int u = ck.x;
+  if (!BFS_IN(p, u, p.n_ni)) return;
   const int64_t rb = p.off[u], re = p.off[u + 1];
   const int64_t beg = rb + (int64_t)ck.y * kChunk;
   const int64_t end = min(beg + kChunk, re);
@@ -586,7 +592,8 @@ __device__ void append_next(const BfsParams& p, int64_t v0, unsigned f, int32_t*
     unsigned long long base = 0;
     if (lane == 31) base = atomicAdd(&slot->qn, (unsigned long long)incl);
     base = __shfl_sync(kFull, base, 31) + (unsigned long long)(incl - c);
-    for (unsigned m = fn; m; m &= m - 1) Q[base++] = (int32_t)(v0 + __ffs(m) - 1);
+    for (unsigned m = fn; m; m &= m - 1, ++base)
+      if (BFS_IN(p, base, p.n_ni)) Q[base] = (int32_t)(v0 + __ffs(m) - 1);
   }
   if (__any_sync(kFull, fd != 0)) {
     long long c = 0;
@@ -603,7 +610,8 @@ __device__ void append_next(const BfsParams& p, int64_t v0, unsigned f, int32_t*
     for (unsigned m = fd; m; m &= m - 1) {
       const int v = (int)(v0 + __ffs(m) - 1);
       const int nc = (int)(((long long)p.deg[v] + kChunk - 1) / kChunk);
-      for (int k = 0; k < nc; ++k) CL[base++] = make_int2(v, k);
+      for (int k = 0; k < nc; ++k, ++base)
+        if (BFS_IN(p, base, p.cl_cap)) CL[base] = make_int2(v, k);
     }
   }
 }
@@ -679,7 +687,7 @@ __device__ bool bu_item(const BfsParams& p, const uint32_t* __restrict__ Vc, uin
       if (!act) continue;
       acc.scanned += 1;
       acc.edges += (unsigned long long)(q ? kB : kA);
-      if (hit >= 0) {
+      if (hit >= 0 && BFS_IN(p, v, p.n_ni)) {
         p.parent_i[v] = q ? cidB : cidA;
         acc.nf += 1;
         acc.mf += (unsigned long long)(q ? hB.deg : hA.deg);
@@ -717,7 +725,7 @@ __device__ bool bu_settle(const BfsParams& p, const uint32_t* __restrict__ Vc, i
   const int lane = lane_id();
   const bool act = lane < cnt;
   const int v = act ? pend[lane] : 0;
-  const HeadRec h = head_load(p, act, v);
+  const HeadRec h = head_load(p, act && BFS_IN(p, v, p.n_ni), v);
   int hit = -1, cid = -1;
   int64_t k = 0;
   if (act) head_probe<false>(p, h, Vc, hit, cid, k);
@@ -729,7 +737,7 @@ __device__ bool bu_settle(const BfsParams& p, const uint32_t* __restrict__ Vc, i
     } else {
       acc.scanned += 1;
       acc.edges += (unsigned long long)k;
-      if (hit >= 0) {
+      if (hit >= 0 && BFS_IN(p, (v >> 5) - w0, 32)) {
         p.parent_i[v] = cid;
         acc.nf += 1;
         acc.mf += (unsigned long long)h.deg;
@@ -774,12 +782,13 @@ __device__ bool bu_dense_item(const BfsParams& p, const uint32_t* __restrict__ V
     for (int u = 0; u < kDenseStep; ++u) {
       un[u] = !((__shfl_sync(kFull, vis, s0 + u) >> lane) & 1u);
       const int v = (int)((w0 + s0 + u) * 32 + lane);
+      un[u] = un[u] && BFS_IN(p, v, p.n_ni);
       a[u] = un[u] ? __ldg(p.lead + v) : make_int2(-1, -1);
       dg[u] = un[u] ? __ldg(p.deg + v) : 0;
     }
     unsigned pw[kDenseStep];
 #pragma unroll
-    for (int u = 0; u < kDenseStep; ++u) pw[u] = a[u].x >= 0 ? Vc[a[u].x >> 5] : 0u;
+    for (int u = 0; u < kDenseStep; ++u) pw[u] = (a[u].x >= 0 && BFS_IN(p, a[u].x, p.n_ni)) ? Vc[a[u].x >> 5] : 0u;
 #pragma unroll
     for (int u = 0; u < kDenseStep; ++u) {
       const int v = (int)((w0 + s0 + u) * 32 + lane);
@@ -953,6 +962,7 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
   WorkCursor wc(nl, gwarp, nwarps, &sc->work2);
   for (long long e = wc.next(); e < nl; e = wc.next()) {
     const int v = p.longq[e];
+    if (!BFS_IN(p, v, p.n_ni)) continue;  // warp-uniform
     const int64_t rb = p.off[v], re = rb + p.deg[v];
     int64_t kv;
     const int hit = warp_scan<false>(p, rb, rb + kHead, re, Vc, kv);
@@ -969,11 +979,13 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
         if (build_next) {  // the next forward level's lists (see append_next)
           LevelSlot* sq = p.slot + ((L + 1) & (kSlots - 1));
           if (v >= p.d) {
-            ((L & 1) ? p.Q0 : p.Q1)[atomicAdd(&sq->qn, 1ull)] = v;
+            const unsigned long long at = atomicAdd(&sq->qn, 1ull);
+            if (BFS_IN(p, at, p.n_ni)) ((L & 1) ? p.Q0 : p.Q1)[at] = v;
           } else {
             const long long nc = ((long long)(re - rb) + kChunk - 1) / kChunk;
             const unsigned long long b = atomicAdd(&sq->nch, (unsigned long long)nc);
-            for (long long k = 0; k < nc; ++k) ((L & 1) ? p.CL0 : p.CL1)[b + k] = make_int2(v, (int)k);
+            for (long long k = 0; k < nc; ++k)
+              if (BFS_IN(p, b + k, p.cl_cap)) ((L & 1) ? p.CL0 : p.CL1)[b + k] = make_int2(v, (int)k);
           }
         }
       }
@@ -1096,9 +1108,10 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
           acc.mf += (unsigned long long)dg;
           if constexpr (kSub) sub_count(p, v, dg, *sacc);
         }
-        if (v >= p.d)
-          Q[qbase + nex + __popc(m & ~dm & ((1u << bit) - 1u))] = v;
-        else
+        if (v >= p.d) {
+          const unsigned long long at = qbase + nex + __popc(m & ~dm & ((1u << bit) - 1u));
+          if (BFS_IN(p, at, p.n_ni)) Q[at] = v;
+        } else
           nc = ((unsigned long long)dg + kChunk - 1) / kChunk;
       }
       if (__any_sync(kFull, nc != 0)) {  // delegates: their row chunks, 32 entries per step
@@ -1122,7 +1135,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
           }
           const int ov = __shfl_sync(kFull, v, o);
           const long long oex = __shfl_sync(kFull, ci, o) - (long long)__shfl_sync(kFull, nc, o);
-          if (e < C) CL[cbase + e] = make_int2(ov, (int)(e - oex));
+          if (e < C && BFS_IN(p, cbase + e, p.cl_cap)) CL[cbase + e] = make_int2(ov, (int)(e - oex));
         }
       }
     }
@@ -1145,8 +1158,9 @@ __device__ void first_level(const BfsParams& p, int s, uint32_t* __restrict__ Vn
   const int64_t rb = p.off[s], re = p.off[s + 1];
   for (int64_t e0 = rb + gwarp * 32; e0 < re; e0 += nwarps * 32) {
     const int64_t e = e0 + lane;
-    const bool act = e < re;
-    const int u = act ? p.col[e] : 0;
+    const int u0 = e < re ? p.col[e] : 0;
+    const bool act = e < re && BFS_IN(p, u0, p.n_ni);
+    const int u = act ? u0 : 0;
     const int dg = act ? p.deg[u] : 0;
     if (act) {
       plane_or(p, u, 1);
@@ -1161,7 +1175,8 @@ __device__ void first_level(const BfsParams& p, int s, uint32_t* __restrict__ Vn
       unsigned long long qb = 0;
       if (lane == 0) qb = atomicAdd(&sn->qn, (unsigned long long)__popc(nm));
       qb = __shfl_sync(kFull, qb, 0);
-      if ((nm >> lane) & 1u) Q[qb + __popc(nm & ((1u << lane) - 1u))] = u;
+      const unsigned long long at = qb + __popc(nm & ((1u << lane) - 1u));
+      if (((nm >> lane) & 1u) && BFS_IN(p, at, p.n_ni)) Q[at] = u;
     }
     const long long nc = (act && u < p.d) ? ((long long)dg + kChunk - 1) / kChunk : 0;
     if (__any_sync(kFull, nc != 0)) {  // delegates: their row chunks, 32 entries per step
@@ -1185,7 +1200,7 @@ __device__ void first_level(const BfsParams& p, int s, uint32_t* __restrict__ Vn
         }
         const int ov = __shfl_sync(kFull, u, o);
         const long long oex = __shfl_sync(kFull, ci, o) - __shfl_sync(kFull, nc, o);
-        if (c < C) CL[cbase + c] = make_int2(ov, (int)(c - oex));
+        if (c < C && BFS_IN(p, cbase + c, p.cl_cap)) CL[cbase + c] = make_int2(ov, (int)(c - oex));
       }
     }
   }
@@ -1846,6 +1861,8 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   p.planes = g->planes;
   p.planes_n = g->planes_n;
   p.pstride = g->pstride;
+  p.cl_cap = g->cl_cap;
+  p.long_cap = g->long_cap;
   p.crank = g->crank;
   p.parent_i = g->parent_i;
   p.Q0 = g->Q0;

@@ -49,6 +49,21 @@ __device__ __forceinline__ void set_failed(const P& p, int code) {
   atomicExch((unsigned*)&p.hdr->err, ((p.epoch & 0x0FFFFFFFu) << 4) | (unsigned)(-code));
 }
 
+// Bounds checks of a BFS_CHECK build: an index outside [0, n) records
+// BFS_ERR_CHECK in the run's status word (never a trap) and the caller skips the
+// access; other builds compile every check to `true`.
+template <class P>
+__device__ __forceinline__ bool check_index(const P& p, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  set_failed(p, BFS_ERR_CHECK);
+  return false;
+}
+#ifdef BFS_CHECK
+#define BFS_IN(p, i, n) ::bfsgb::check_index((p), (long long)(i), (long long)(n))
+#else
+#define BFS_IN(p, i, n) true
+#endif
+
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");

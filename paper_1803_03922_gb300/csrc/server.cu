@@ -3,10 +3,11 @@
 // the runtime that turns the 64-lane multi-source kernel into a query server.
 //
 // Threads: callers submit and poll under `mu`; one worker thread owns the batch
-// contexts and does every CUDA call of the server; a host function queued on a
-// context's stream after its launch stamps the completion time and wakes the
-// worker.  The worker never holds `mu` across a CUDA call (cudaFree and friends
-// wait for queued host functions, which take `mu`).
+// contexts and does every CUDA call of the server.  An event recorded after each
+// launch marks its end: while launches are in flight the worker polls their
+// events and the submission queue without sleeping (a query's completion and a
+// new query's launch cost no thread wake-up); with nothing in flight it waits for
+// a submission.  The worker never holds `mu` across a CUDA call.
 //
 // Scheduling: one FIFO per graph.  While fewer than max_concurrent launches run,
 // the graph whose oldest waiting query arrived first gets one launch of up to
@@ -41,7 +42,6 @@ namespace {
 constexpr int kMaxLanes = 64;
 constexpr int kMaxConcurrent = 8;
 constexpr int kMaxSingle = 4;  // single-source runs per launch of a graph's level-loop context
-constexpr int64_t kStuckCheckNs = 1000000000;  // query a silent stream after 1 s
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -75,7 +75,7 @@ struct Context {
   std::vector<Query> q;  // the queries of the launch in flight
   unsigned epoch[kMaxSingle] = {0, 0, 0, 0};
   int64_t t_launch = 0;
-  std::atomic<int64_t> t_done{0};  // stamped by the stream's host function; 0 while running
+  cudaEvent_t ev = nullptr;  // recorded after the launch: its end
 };
 
 bool device_ptr(const void* q) {
@@ -111,17 +111,6 @@ struct bfs_server {
 };
 
 namespace {
-
-void CUDART_CB on_launch_done(void* arg) {  // runs on a CUDA thread: no CUDA calls here
-  Context* c = static_cast<Context*>(arg);
-  c->t_done.store(now_ns(), std::memory_order_release);
-  bfs_server* s = c->srv;
-  {
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->wake = true;
-  }
-  s->cv_work.notify_one();
-}
 
 // Moves the queries of a finished launch to the done list.  status: the launch's
 // own failure, or BFS_OK to take each query's status from its run header (one
@@ -162,20 +151,21 @@ void finish(bfs_server* s, Context& c, int status, int64_t t_done) {
   s->cv_done.notify_all();
 }
 
-void reap(bfs_server* s) {
-  const int64_t now = now_ns();
+// Finishes every launch whose end event has completed; returns how many.
+int reap(bfs_server* s) {
+  int n = 0;
   for (auto& cp : s->ctx) {
     Context& c = *cp;
     if (!c.busy) continue;
-    const int64_t td = c.t_done.load(std::memory_order_acquire);
-    if (td) {
-      finish(s, c, BFS_OK, td);
-    } else if (now - c.t_launch > kStuckCheckNs) {
-      // a stream whose work failed never runs its host function
-      const cudaError_t e = cudaStreamQuery(c.stream);
-      if (e != cudaSuccess && e != cudaErrorNotReady) finish(s, c, cuda_fail(e, "serving launch"), now_ns());
-    }
+    const cudaError_t e = cudaEventQuery(c.ev);
+    if (e == cudaErrorNotReady) continue;
+    if (e == cudaSuccess)
+      finish(s, c, BFS_OK, now_ns());
+    else
+      finish(s, c, cuda_fail(e, "serving launch"), now_ns());
+    ++n;
   }
+  return n;
 }
 
 bool admit(bfs_server* s, int64_t bytes) {
@@ -196,6 +186,7 @@ bool admit(bfs_server* s, int64_t bytes) {
 void drop_context(bfs_server* s, size_t i) {
   Context& c = *s->ctx[i];
   if (c.b) bfs_batch_free(c.b);
+  if (c.ev) cudaEventDestroy(c.ev);
   if (c.stream) cudaStreamDestroy(c.stream);
   if (c.hdr) cudaFreeHost(c.hdr);
   {
@@ -211,8 +202,10 @@ Context* new_context(bfs_server* s, int gid) {
   c->srv = s;
   c->gid = gid;
   if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost((void**)&c->hdr, kMaxSingle * sizeof(RunHeader)) != cudaSuccess) {
     cudaGetLastError();
+    if (c->ev) cudaEventDestroy(c->ev);
     if (c->stream) cudaStreamDestroy(c->stream);
     return nullptr;
   }
@@ -281,7 +274,6 @@ void launch(bfs_server* s, Context& c) {
     pl[j] = c.q[j].parent;
   }
   c.busy = true;
-  c.t_done.store(0, std::memory_order_relaxed);
   c.t_launch = now_ns();
   int rc;
   if (c.single) {
@@ -305,9 +297,9 @@ void launch(bfs_server* s, Context& c) {
     rc = bfsgb::ms_launch(c.b, src, k, dl, s->opt.with_parents ? pl : nullptr, c.stream, c.hdr, &c.epoch[0]);
   }
   if (rc == BFS_OK) {
-    const cudaError_t e = cudaLaunchHostFunc(c.stream, on_launch_done, &c);
+    const cudaError_t e = cudaEventRecord(c.ev, c.stream);
     if (e == cudaSuccess) return;
-    rc = cuda_fail(e, "queue completion callback");
+    rc = cuda_fail(e, "record the launch's end");
   }
   cudaStreamSynchronize(c.stream);  // runs already queued finish before the context is reused
   finish(s, c, rc, now_ns());
@@ -378,6 +370,12 @@ void worker_main(bfs_server* s) {
     schedule(s);
     std::unique_lock<std::mutex> lk(s->mu);
     if (s->stop && s->in_flight == 0) break;
+    if (s->in_flight > 0) {  // poll the launches' end events and the queue
+      s->wake = false;
+      lk.unlock();
+      std::this_thread::yield();
+      continue;
+    }
     s->cv_work.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->wake; });
     s->wake = false;
   }
