@@ -217,8 +217,8 @@ typedef struct bfs_batch bfs_batch;
 #define BFS_BATCH_LOG_LEVELS 64
 
 typedef struct bfs_batch_level {
-  int32_t direction;          /* 1 if any query's lane pulls (backward) at this level, else 0 */
-  int32_t pulled_lanes;       /* lanes that pull; the other lanes with a frontier push (forward) */
+  int32_t direction;          /* 0 forward (push), 1 backward (pull), for all lanes alike */
+  int32_t pulled_lanes;       /* lanes with a frontier at a backward level (they all pull), else 0 */
   int64_t frontier_vertices;  /* vertices in the union of the queries' frontiers */
   int64_t frontier_edges;     /* their degree sum */
   int64_t pairs;              /* (query, vertex) pairs in the frontier */

@@ -49,7 +49,7 @@ struct __align__(16) MsDefer {
 constexpr int kMsHead = 512;
 
 struct MsLog {
-  int32_t dir, pad;
+  int32_t dir, pad;  // pad: lanes that pull at a backward level
   unsigned long long nfv, mfv, pairs, t_begin, t_expand, t_end;
 };
 
@@ -606,6 +606,7 @@ __global__ void __launch_bounds__(kThreads, 2) ms_bfs_loop(MsParams p) {
       if (L < BFS_BATCH_LOG_LEVELS) {
         MsLog& lg = p.log[L];
         lg.dir = bu ? 1 : 0;
+        lg.pad = bu ? popc_w((W)__ldcg(&sc->aux)) : 0;
         lg.nfv = __ldcg(&sc->nfv);
         lg.mfv = __ldcg(&sc->mfv);
         lg.pairs = __ldcg(&sc->pairs);
@@ -945,6 +946,7 @@ extern "C" int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, ui
           for (int L = 0; L < stats->logged_levels; ++L) {
             bfs_batch_level& o = stats->level[L];
             o.direction = lg[L].dir;
+            o.pulled_lanes = lg[L].pad;
             o.frontier_vertices = (int64_t)lg[L].nfv;
             o.frontier_edges = (int64_t)lg[L].mfv;
             o.pairs = (int64_t)lg[L].pairs;
