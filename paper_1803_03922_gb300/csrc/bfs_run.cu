@@ -1701,92 +1701,111 @@ __global__ void k_deg_del(const int64_t* __restrict__ off, const int32_t* __rest
   if (threadIdx.x < 3 && s_t[threadIdx.x]) atomicAdd(&tot[threadIdx.x], s_t[threadIdx.x]);
 }
 
-// Results in caller ids, 4 consecutive caller ids per thread: a kernel of its
-// own, launched after the level loop on the same stream (L = levels run).
+// One quad of results (caller ids 4q .. 4q+3) in the output form of the run.
+__device__ __forceinline__ void write_quad(const BfsParams& p, int64_t q, const int (&dv)[4], const int (&pv)[4]) {
+  const int64_t c = q * 4;
+  if (p.out_depth8) {  // uint8 form: 255 = unreached
+    unsigned d8 = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (dv[t] > 254) set_failed(p, BFS_ERR_OVERFLOW);
+      d8 |= (unsigned)(dv[t] < 0 ? 255 : (dv[t] & 0xFF)) << (8 * t);
+    }
+    if (p.out_vec4 && c + 3 < p.n) {
+      reinterpret_cast<unsigned*>(p.out_depth8)[q] = d8;
+      if (p.out_parent) reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (c + t < p.n) {
+          p.out_depth8[c + t] = (uint8_t)(d8 >> (8 * t));
+          if (p.out_parent) p.out_parent[c + t] = pv[t];
+        }
+    }
+  } else if (p.out_vec4 && c + 3 < p.n) {
+    reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
+    reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (c + t < p.n) {
+        p.out_depth[c + t] = dv[t];
+        p.out_parent[c + t] = pv[t];
+      }
+  }
+}
+
+// Results in caller ids: a kernel of its own, launched after the level loop on
+// the same stream.  A caller id's internal id comes from its word of the
+// caller-rank table (which of the word's callers are delegates / non-isolated
+// normal vertices, and how many of each precede the word: both classes are
+// numbered in caller order); isolated vertices are never reached but the
+// source.  The depth is the vertex's nibbles, zero meaning unreached (the source
+// is set apart).  A thread takes kResultQuads quads of 4 consecutive caller ids
+// per step, their loads all in flight before the first is used.
+constexpr int kResultQuads = 2;
 
 __global__ void __launch_bounds__(kThreads) bfs_results(BfsParams p) {
   if (run_failed(p)) return;  // outputs are unspecified after a failed run
   const int L = *(volatile int*)&p.hdr->levels_run;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
-  // A caller id's internal id comes from its word of the caller-rank table
-  // (which of the word's callers are delegates / non-isolated normal vertices,
-  // and how many of each precede the word: both classes are numbered in caller
-  // order); isolated vertices are never reached but the source.  The depth is
-  // the vertex's nibbles; zero means unreached (the source is set apart).
   // nibble planes that hold a depth of this run: the last level run found
   // nothing, so the deepest vertex is at depth L - 1
   int nib_used = 1;
   while (nib_used < p.planes_n && ((L - 1) >> (4 * nib_used)) > 0) ++nib_used;
   const int64_t C4 = ((int64_t)p.n + 3) / 4;
-  for (int64_t q = gtid; q < C4; q += gthreads) {
-    const int4 rk = p.crank[q >> 3];
-    const int b0 = (int)((q & 7) * 4);
-    int vs[4];
+  constexpr int U = kResultQuads;
+  for (int64_t q0 = gtid; q0 < C4; q0 += gthreads * U) {
+    int vs[U][4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int b = b0 + t;
-      const unsigned lo = (1u << b) - 1u;
-      int v = -1;
-      if (((unsigned)rk.x >> b) & 1u)
-        v = rk.z + __popc((unsigned)rk.x & lo);
-      else if (((unsigned)rk.y >> b) & 1u)
-        v = p.d + rk.w + __popc((unsigned)rk.y & lo);
-      vs[t] = v;
-    }
-    // the depth word and the parent slot of every non-isolated vertex are loaded
-    // together (almost all of them are reached), so a quad costs two round trips
-    unsigned nw[4];
-    int pp[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      nw[t] = vs[t] >= 0 ? p.planes[vs[t] >> 3] : 0u;
-      pp[t] = vs[t] >= 0 ? p.parent_i[vs[t]] : -1;
-    }
-    int dv[4], pv[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int v = vs[t];
-      int dd = v >= 0 ? (int)((nw[t] >> (4 * (v & 7))) & 15u) : 0;
-      for (int k = 1; k < nib_used && v >= 0; ++k)
-        dd |= (int)((p.planes[(int64_t)k * p.pstride + (v >> 3)] >> (4 * (v & 7))) & 15u) << (4 * k);
-      const bool r = dd > 0;
-      dv[t] = r ? dd : -1;
-      pv[t] = r ? pp[t] : -1;
-      if (q * 4 + t == p.src_c) {
-        dv[t] = 0;
-        pv[t] = p.src_c;
-      }
-    }
-    const int64_t c = q * 4;
-    if (p.out_depth8) {  // uint8 form: 255 = unreached
-      unsigned d8 = 0;
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = q0 + (int64_t)u * gthreads;
+      const int4 rk = q < C4 ? p.crank[q >> 3] : make_int4(0, 0, 0, 0);
+      const int b0 = (int)((q & 7) * 4);
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        if (dv[t] > 254) set_failed(p, BFS_ERR_OVERFLOW);
-        d8 |= (unsigned)(dv[t] < 0 ? 255 : (dv[t] & 0xFF)) << (8 * t);
+        const int b = b0 + t;
+        const unsigned lo = (1u << b) - 1u;
+        int v = -1;
+        if (((unsigned)rk.x >> b) & 1u)
+          v = rk.z + __popc((unsigned)rk.x & lo);
+        else if (((unsigned)rk.y >> b) & 1u)
+          v = p.d + rk.w + __popc((unsigned)rk.y & lo);
+        vs[u][t] = v;
       }
-      if (p.out_vec4 && c + 3 < p.n) {
-        reinterpret_cast<unsigned*>(p.out_depth8)[q] = d8;
-        if (p.out_parent) reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
-      } else {
+    }
+    // the depth word and the parent slot of every non-isolated vertex are loaded
+    // together (almost all of them are reached)
+    unsigned nw[U][4];
+    int pp[U][4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (c + t < p.n) {
-            p.out_depth8[c + t] = (uint8_t)(d8 >> (8 * t));
-            if (p.out_parent) p.out_parent[c + t] = pv[t];
-          }
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        nw[u][t] = vs[u][t] >= 0 ? p.planes[vs[u][t] >> 3] : 0u;
+        pp[u][t] = vs[u][t] >= 0 ? p.parent_i[vs[u][t]] : -1;
       }
-    } else if (p.out_vec4 && c + 3 < p.n) {
-      reinterpret_cast<int4*>(p.out_depth)[q] = make_int4(dv[0], dv[1], dv[2], dv[3]);
-      reinterpret_cast<int4*>(p.out_parent)[q] = make_int4(pv[0], pv[1], pv[2], pv[3]);
-    } else {
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (c + t < p.n) {
-          p.out_depth[c + t] = dv[t];
-          p.out_parent[c + t] = pv[t];
+    for (int u = 0; u < U; ++u) {
+      const int64_t q = q0 + (int64_t)u * gthreads;
+      if (q >= C4) break;
+      int dv[4], pv[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int v = vs[u][t];
+        int dd = v >= 0 ? (int)((nw[u][t] >> (4 * (v & 7))) & 15u) : 0;
+        for (int k = 1; k < nib_used && v >= 0; ++k)
+          dd |= (int)((p.planes[(int64_t)k * p.pstride + (v >> 3)] >> (4 * (v & 7))) & 15u) << (4 * k);
+        const bool r = dd > 0;
+        dv[t] = r ? dd : -1;
+        pv[t] = r ? pp[u][t] : -1;
+        if (q * 4 + t == p.src_c) {
+          dv[t] = 0;
+          pv[t] = p.src_c;
         }
+      }
+      write_quad(p, q, dv, pv);
     }
   }
   __syncthreads();
