@@ -410,6 +410,14 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
   // caller order, and rows are sorted by caller id): their discovered bits are
   // OR-ed together and set with one atomic per run of equal words
   unsigned rw = 0xFFFFFFFFu, rb = 0u;
+  // the targets' parent slots are read first and only a smaller offer is sent:
+  // a hub frontier offers each delegate target several parents, and the L2's
+  // atomic rate bounds such a level; a stale read only costs an extra atomic
+  // (parents only decrease)
+  int pcur[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    pcur[t] = (v[t] >= 0 && !((vw[t] >> (v[t] & 31)) & 1u) && p.td_parent == BFS_TD_PARENT_ATOMICMIN) ? __ldcg(p.parent_i + v[t]) : INT_MIN;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if (v[t] < 0 || ((vw[t] >> (v[t] & 31)) & 1u)) continue;
@@ -417,7 +425,7 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
       if (!((v[t] < p.d) ? (allow & 1u) : (allow & 2u))) continue;
     }
     found = true;
-    if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], pcaller);
+    if (pcur[t] > pcaller) atomicMin(p.parent_i + v[t], pcaller);
     const unsigned w = (unsigned)v[t] >> 5, bit = 1u << (v[t] & 31);
     if (w != rw) {
       if (rb) atomicOr(N + rw, rb);
@@ -1742,10 +1750,12 @@ __device__ __forceinline__ void write_quad(const BfsParams& p, int64_t q, const 
 // numbered in caller order); isolated vertices are never reached but the
 // source.  The depth is the vertex's nibbles, zero meaning unreached (the source
 // is set apart).  A thread takes kResultQuads quads of 4 consecutive caller ids
-// per step, their loads all in flight before the first is used.
-constexpr int kResultQuads = 2;
+// per step, their loads all in flight before the first is used; at 32
+// registers four 512-thread CTAs fit an SM (RMAT-26: 162 us against 177 us with
+// two quads per thread at two CTAs per SM).
+constexpr int kResultQuads = 1;
 
-__global__ void __launch_bounds__(kThreads) bfs_results(BfsParams p) {
+__global__ void __launch_bounds__(kThreads, 4) bfs_results(BfsParams p) {
   if (run_failed(p)) return;  // outputs are unspecified after a failed run
   const int L = *(volatile int*)&p.hdr->levels_run;
   const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1944,8 +1954,9 @@ int launch_run(bfs_graph* g, int32_t source, int32_t* out_depth, int32_t* out_pa
   const int threads = (!sub && g->variant == 1) ? 2 * kThreads : kThreads;
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
   if (e != cudaSuccess) return cuda_fail(e, "level-loop launch");
-  // the results, on the same CTAs' worth of the device (a serving slice stays a slice)
-  const int rblocks = blocks * threads / kThreads;
+  // the results, on the same SMs (a serving slice stays a slice): four result
+  // CTAs per SM where the loop has two
+  const int rblocks = blocks * threads / kThreads * 2;
   bfs_results<<<rblocks, kThreads, 0, s>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "result-pass launch");
