@@ -426,6 +426,8 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
     }
     found = true;
     if (pcur[t] > pcaller) atomicMin(p.parent_i + v[t], pcaller);
+    // a parent slot already offered at this level: its first offerer sets the bit
+    if (!kSub && pcur[t] != INT_MAX && pcur[t] != INT_MIN) continue;
     const unsigned w = (unsigned)v[t] >> 5, bit = 1u << (v[t] & 31);
     if (w != rw) {
       if (rb) atomicOr(N + rw, rb);
@@ -474,10 +476,15 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
     // target (most edges of a late forward level meet visited vertices)
     if (v >= 0 && !((Vc[(unsigned)v >> 5] >> (v & 31)) & 1u)) {
       found = true;
-      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v, p.caller_of[ou]);
+      int pcur = INT_MAX;
+      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
+        pcur = __ldcg(p.parent_i + v);
+        const int pc = p.caller_of[ou];
+        if (pcur > pc) atomicMin(p.parent_i + v, pc);
+      }
       const unsigned bit = 1u << (v & 31);
       uint32_t* nw = N + ((unsigned)v >> 5);
-      if (!(p.tuning & 1) || !(__ldcg(nw) & bit)) atomicOr(nw, bit);
+      if ((kSub || pcur == INT_MAX) && (!(p.tuning & 1) || !(__ldcg(nw) & bit))) atomicOr(nw, bit);
     }
   }
 }
