@@ -1018,7 +1018,8 @@ __device__ void drain_long_rows(const BfsParams& p, const uint32_t* __restrict__
 // then handles the item's new vertices 32 at a time (rank -> word by a binary
 // search over the lanes' prefixes, bit by rank within the word).  With `merge`,
 // also writes the next visited bitmap Vn = Vc | Nsrc and clears Nclr.  With `count` (after a forward level),
-// also writes depth `depth` for every new vertex and adds n_f and m_f.
+// also writes depth `depth` for every new vertex and adds n_f and m_f.  With Q
+// null, no lists are written (a later conversion pass builds them).
 // Counters of the per-subgraph schedule over a set of vertices (LevelSlot::sub).
 struct SubAcc {
   unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
@@ -1099,7 +1100,7 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
     const int T = __shfl_sync(kFull, incl, 31), Tn = __shfl_sync(kFull, nincl, 31);
     const int excl = incl - cnt, nexcl = nincl - ncnt;
     unsigned long long qbase = 0;
-    if (lane == 0 && Tn) qbase = atomicAdd(&slot->qn, (unsigned long long)Tn);
+    if (Q && lane == 0 && Tn) qbase = atomicAdd(&slot->qn, (unsigned long long)Tn);
     qbase = __shfl_sync(kFull, qbase, 0);
     for (int k0 = 0; k0 < T; k0 += 32) {
       const int k = k0 + lane;
@@ -1123,7 +1124,8 @@ __device__ void frontier_from_bitmap(const BfsParams& p, const uint32_t* __restr
           acc.mf += (unsigned long long)dg;
           if constexpr (kSub) sub_count(p, v, dg, *sacc);
         }
-        if (v >= p.d) {
+        if (!Q) {  // counts only
+        } else if (v >= p.d) {
           const unsigned long long at = qbase + nex + __popc(m & ~dm & ((1u << bit) - 1u));
           if (BFS_IN(p, at, p.n_ni)) Q[at] = v;
         } else
@@ -1564,6 +1566,11 @@ __device__ void run_body(const BfsParams& p) {
       if (grid_sync(p, seq, no_master) < 0) return;
     }
     if (leader) s_tb = gtimer();
+    // A big forward level (more frontier entries than bitmap words) usually
+    // hands over to a backward level: its sweep leaves the next lists to a
+    // conversion pass at the start of the next level, run only if that level
+    // is forward too.
+    bool defer_lists = false;
     // The barrier master's step once the level's counters are complete: the
     // direction of level L+1, and this level's log counters (loaded together).
     auto master = [&](int) {
@@ -1584,8 +1591,8 @@ __device__ void run_body(const BfsParams& p) {
       // a backward level with few unvisited vertices left builds the next
       // forward level's lists as it goes, so a switch back needs no conversion
       const int lists = (nd && s_unv * kListsFraction < (long long)p.n_ni) ? kBitLists : 0;
-      return (nd ? kBitBackward : 0) | ((nd == 0 && dir == 1) ? kBitConvert : 0) | iw_code(s_unv, p) | lists |
-             (nd ? dense_bit(s_unv, p) : 0);
+      return (nd ? kBitBackward : 0) | ((nd == 0 && (dir == 1 || defer_lists)) ? kBitConvert : 0) |
+             iw_code(s_unv, p) | lists | (nd ? dense_bit(s_unv, p) : 0);
     };
     if (dir == 0 && L == 0 && p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
       first_level(p, src_i, Vn, Ncur, p.Q1, p.CL1, sn, acc);
@@ -1611,9 +1618,11 @@ __device__ void run_body(const BfsParams& p) {
         bits = eb;
         ended = true;
       } else {
-        // the next frontier's queues, depths and counts; Vn = Vc | N
-        frontier_from_bitmap(p, Vc, Vn, Ncur, Noth, (L & 1) ? p.Q0 : p.Q1, (L & 1) ? p.CL0 : p.CL1, sn, true,
-                             true, L + 1, acc);
+        // the next frontier's depths and counts (and its lists, when parents are
+        // pulled); Vn = Vc | N
+        defer_lists = p.td_parent != BFS_TD_PARENT_PULL && __ldcg(&sc->m_f) > (unsigned long long)p.words;
+        frontier_from_bitmap(p, Vc, Vn, Ncur, Noth, defer_lists ? nullptr : ((L & 1) ? p.Q0 : p.Q1),
+                             (L & 1) ? p.CL0 : p.CL1, sn, true, true, L + 1, acc);
         flush_block(acc, &sn->n_f, &sn->m_f, nullptr, nullptr, nullptr);
         if (p.td_parent == BFS_TD_PARENT_PULL) {
           if (grid_sync(p, seq, no_master) < 0) return;  // the queues of F_{L+1} are complete
