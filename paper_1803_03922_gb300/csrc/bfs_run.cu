@@ -456,35 +456,51 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
   const int64_t incl = warp_incl_scan(deg);
   const int64_t total = __shfl_sync(kFull, incl, 31);
   const int64_t excl = incl - deg;
-  for (int64_t base = 0; base < total; base += 32) {
-    const int64_t e = base + lane;
-    int pos = 0;
+  // up to four entries per lane per step (entries base + lane + 32 t), their
+  // column loads, probes and parent reads in flight together
+  for (int64_t base = 0; base < total; base += 128) {
+    int v[4], ou[4];
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-      const int64_t t = __shfl_sync(kFull, incl, pos + s - 1);
-      if (t <= e) pos += s;
+    for (int t = 0; t < 4; ++t) {
+      const int64_t e = base + lane + 32 * t;
+      int pos = 0;
+#pragma unroll
+      for (int s = 16; s >= 1; s >>= 1) {
+        const int64_t x = __shfl_sync(kFull, incl, pos + s - 1);
+        if (x <= e) pos += s;
+      }
+      const int64_t ob = __shfl_sync(kFull, beg, pos);
+      const int64_t ox = __shfl_sync(kFull, excl, pos);
+      ou[t] = __shfl_sync(kFull, u, pos);
+      v[t] = (e < total && BFS_IN(p, ob + (e - ox), p.nnz)) ? p.col[ob + (e - ox)] : -1;
     }
-    const int64_t ob = __shfl_sync(kFull, beg, pos);
-    const int64_t ox = __shfl_sync(kFull, excl, pos);
-    const int ou = __shfl_sync(kFull, u, pos);
-    int v = (e < total && BFS_IN(p, ob + (e - ox), p.nnz)) ? p.col[ob + (e - ox)] : -1;
-    if (v >= 0 && !BFS_IN(p, v, p.n_ni)) v = -1;
-    if constexpr (kSub) {  // per-subgraph directions: only targets of the classes in allow
-      if (v >= 0 && !((v < p.d) ? (allow & 1u) : (allow & 2u))) v = -1;
+    unsigned un = 0;  // bit t: entry t meets an unvisited target
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (v[t] >= 0 && !BFS_IN(p, v[t], p.n_ni)) v[t] = -1;
+      if constexpr (kSub) {  // per-subgraph directions: only targets of the classes in allow
+        if (v[t] >= 0 && !((v[t] < p.d) ? (allow & 1u) : (allow & 2u))) v[t] = -1;
+      }
+      if (v[t] >= 0 && !((Vc[(unsigned)v[t] >> 5] >> (v[t] & 31)) & 1u)) un |= 1u << t;
     }
+    if (!un) continue;
+    found = true;
     // the frontier vertex's caller id is loaded only for an edge into an unvisited
     // target (most edges of a late forward level meet visited vertices)
-    if (v >= 0 && !((Vc[(unsigned)v >> 5] >> (v & 31)) & 1u)) {
-      found = true;
-      int pcur = INT_MAX;
-      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) {
-        pcur = __ldcg(p.parent_i + v);
-        const int pc = p.caller_of[ou];
-        if (pcur > pc) atomicMin(p.parent_i + v, pc);
-      }
-      const unsigned bit = 1u << (v & 31);
-      uint32_t* nw = N + ((unsigned)v >> 5);
-      if ((kSub || pcur == INT_MAX) && (!(p.tuning & 1) || !(__ldcg(nw) & bit))) atomicOr(nw, bit);
+    int pcur[4], pc[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const bool a = ((un >> t) & 1u) && p.td_parent == BFS_TD_PARENT_ATOMICMIN;
+      pcur[t] = a ? __ldcg(p.parent_i + v[t]) : INT_MAX;
+      pc[t] = a ? p.caller_of[ou[t]] : INT_MAX;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (!((un >> t) & 1u)) continue;
+      if (pcur[t] > pc[t]) atomicMin(p.parent_i + v[t], pc[t]);
+      const unsigned bit = 1u << (v[t] & 31);
+      uint32_t* nw = N + ((unsigned)v[t] >> 5);
+      if ((kSub || pcur[t] == INT_MAX) && (!(p.tuning & 1) || !(__ldcg(nw) & bit))) atomicOr(nw, bit);
     }
   }
 }
