@@ -808,7 +808,8 @@ def serving_extras(stream):
 
 def config_of(name, w, info=None):
     c = {"workload": name, "graph": "RMAT" if w["kind"] == "rmat" else "Erdos-Renyi", "scale": w["scale"],
-         "n": 1 << w["scale"], "th": w["th"], "alpha": 15, "beta": 18, "sources": N_SOURCES,
+         "n": 1 << w["scale"], "th": w["th"], "schedule": "beamer_stay", "alpha": 15, "beta": 18,
+         "sources": N_SOURCES,
          "graph_seed": w["seed"], "source_seed": w["src_seed"],
          "l2": "inputs larger than L2 and L2 flushed (256 MiB write) before every timed run"}
     if w["kind"] == "rmat":

@@ -51,6 +51,9 @@ struct CUstream_st; /* cudaStream_t is `struct CUstream_st*` */
 #define BFS_SCHED_ALTERNATE 3 /* even levels forward, odd levels backward */
 #define BFS_SCHED_MASK 4      /* level L backward iff bit min(L,63) of schedule_mask is set */
 #define BFS_SCHED_PAPER 5     /* Sec. IV-B workload rule: FV vs factor * BV, BV = |U|(q+s)/q */
+#define BFS_SCHED_BEAMER_STAY 7 /* the default: BFS_SCHED_BEAMER, except that BU->TD also needs
+                                  m_f*alpha <= m_u (a level with few unvisited vertices left stays
+                                  backward however small its frontier); not in the paper */
 #define BFS_SCHED_PAPER_SUBGRAPH 6 /* Sec. IV-B per subgraph: the dd, dn and nd visits each take their own
                                       direction by the FV/BV rule with their own factor pair
                                       (subgraph_factor0/1); nn is always forward.  Per subgraph X:
@@ -67,7 +70,7 @@ struct CUstream_st; /* cudaStream_t is `struct CUstream_st*` */
 typedef struct bfs_options {
   int64_t th;               /* degree threshold TH (>= 0): delegates have degree > th. Build-time. */
   int32_t edges_on_device;  /* bfs_build_graph: 1 if src/dst are device pointers, 0 if host. */
-  int32_t schedule;         /* BFS_SCHED_* */
+  int32_t schedule;         /* BFS_SCHED_* (default BFS_SCHED_BEAMER_STAY) */
   uint64_t schedule_mask;   /* for BFS_SCHED_MASK */
   int32_t alpha;            /* Beamer alpha (default 15) */
   int32_t beta;             /* Beamer beta (default 18) */

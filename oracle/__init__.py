@@ -182,12 +182,12 @@ class Graph:
 
     def directions(self, s: int, depth, rule: str = "beamer", alpha: int = 15, beta: int = 18,
                    factor0: float = 0.5, factor1: float = 1e-7):
-        """Per-level directions (0 forward, 1 backward) that the rule ("beamer" or
-        "paper", Sec. IV-B) takes on the run from s with final depth `depth`."""
+        """Per-level directions (0 forward, 1 backward) that the rule ("beamer",
+        "beamer_stay" or "paper", Sec. IV-B) takes on the run from s with final depth `depth`."""
         depth = np.ascontiguousarray(depth, dtype=np.int32)
         cap = int(depth.max()) + 2 if depth.size else 1
         out = np.zeros(cap, dtype=np.int32)
-        code = {"beamer": 0, "paper": 1}[rule]
+        code = {"beamer": 0, "paper": 1, "beamer_stay": 2}[rule]
         rc = self._lib.orc_directions(self._h, int(s), _ptr(depth), code, int(alpha), int(beta), float(factor0),
                                       float(factor1), cap, _ptr(out))
         if rc < 0:

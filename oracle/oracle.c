@@ -322,7 +322,7 @@ int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int6
 int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t rule, int64_t alpha, int64_t beta,
                    double factor0, double factor1, int32_t max_levels, int32_t* dirs) {
   if (!g || !depth || !dirs || s < 0 || s >= g->n || max_levels < 0) return ORC_ERR_INVALID;
-  if (rule != ORC_RULE_BEAMER && rule != ORC_RULE_PAPER) return ORC_ERR_INVALID;
+  if (rule != ORC_RULE_BEAMER && rule != ORC_RULE_PAPER && rule != ORC_RULE_BEAMER_STAY) return ORC_ERR_INVALID;
   if (g->off[s + 1] == g->off[s]) return 0; /* isolated source: no level runs */
   int32_t levels = 0;
   int64_t n_ni = 0;
@@ -362,6 +362,7 @@ int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t 
       next = fv[L] * alpha > m_u;
     } else {
       next = !(q[L] * beta < (int64_t)g->n && q[L] < q_prev);
+      if (rule == ORC_RULE_BEAMER_STAY && fv[L] * alpha > m_u) next = 1;
     }
     cur = next ? 1 : 0;
     if (L < max_levels) dirs[L] = cur;

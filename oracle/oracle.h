@@ -102,6 +102,7 @@ int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int6
 
 #define ORC_RULE_BEAMER 0
 #define ORC_RULE_PAPER 1
+#define ORC_RULE_BEAMER_STAY 2
 
 /* Visit directions a direction rule takes on the run from s, given that run's
  * final depth.  The direction of level L (which expands F_L, the vertices at
@@ -117,6 +118,10 @@ int orc_level_counters(const orc_graph* g, int32_t s, const int32_t* depth, int6
  * ORC_RULE_BEAMER (Beamer's rule, which the paper's DO follows, Sec. II-C):
  *   forward turns backward when alpha * FV > m_u; backward turns forward when
  *   beta * q < n and q < q_prev.
+ * ORC_RULE_BEAMER_STAY (this build's default; not in the paper): Beamer's rule,
+ *   except that backward turns forward only when, besides Beamer's test, the
+ *   forward-to-backward test fails too (alpha * FV <= m_u): a level with few
+ *   unvisited vertices left stays backward however small its frontier.
  * Writes dirs[L] (0 forward, 1 backward) for L < levels = max depth + 1, at
  * most max_levels of them; returns levels (0 for an isolated source) or an error. */
 int orc_directions(const orc_graph* g, int32_t s, const int32_t* depth, int32_t rule, int64_t alpha, int64_t beta,

@@ -35,6 +35,7 @@ BFS_SCHED_ALTERNATE = 3
 BFS_SCHED_MASK = 4
 BFS_SCHED_PAPER = 5
 BFS_SCHED_PAPER_SUBGRAPH = 6
+BFS_SCHED_BEAMER_STAY = 7
 
 BFS_TD_PARENT_PULL = 0
 BFS_TD_PARENT_ATOMICMIN = 1

@@ -44,7 +44,7 @@ def th_space_for_scale(scale: int):
     neighbours a factor 2 away."""
     t = th_for_scale(scale)
     return tuple(sorted(set(TH_SPACE) | {max(1, t // 2), t, 2 * t}))
-BEAMER, PAPER, MASK = 0, 5, 4
+BEAMER, PAPER, MASK, BEAMER_STAY = 0, 5, 4, 7
 
 
 @dataclasses.dataclass
@@ -118,7 +118,7 @@ def tune(evaluate_for_th: Callable[[int], Callable[[Dict[str, object]], float]],
     """Full search.  evaluate_for_th(th) returns an evaluate(options) for a graph
     built with that threshold; directions_for_th(th, options) returns the
     per-level directions the options produce on a representative source."""
-    defaults = dict(defaults or {"schedule": BEAMER, "alpha": 15, "beta": 18, "blocks_per_sm": 2})
+    defaults = dict(defaults or {"schedule": BEAMER_STAY, "alpha": 15, "beta": 18, "blocks_per_sm": 2})
     trials: list = []
     baseline_t = None
     per_th = {}

@@ -57,7 +57,7 @@ int dmalloc(T** p, size_t count, int64_t* total, const char* what) {
 
 int check_options(const bfs_options& o) {
   if (o.th < 0) return fail(BFS_ERR_INVALID, "th must be >= 0");
-  if (o.schedule < BFS_SCHED_BEAMER || o.schedule > BFS_SCHED_PAPER_SUBGRAPH)
+  if (o.schedule < BFS_SCHED_BEAMER || o.schedule > BFS_SCHED_BEAMER_STAY)
     return fail(BFS_ERR_INVALID, "unknown schedule");
   for (int i = 0; i < 3; ++i)
     if (!(o.subgraph_factor0[i] >= 0) || !(o.subgraph_factor1[i] >= 0))
@@ -199,7 +199,7 @@ extern "C" int bfs_options_default(bfs_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->th = 64;
   opt->edges_on_device = 0;
-  opt->schedule = BFS_SCHED_BEAMER;
+  opt->schedule = BFS_SCHED_BEAMER_STAY;
   opt->schedule_mask = 0;
   opt->alpha = 15;
   opt->beta = 18;

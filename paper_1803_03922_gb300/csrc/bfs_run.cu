@@ -1295,10 +1295,12 @@ __device__ int decide(const BfsParams& p, int L1, int cur, unsigned long long nf
       if (cur == 0) return fv > p.factor0 * bv ? 1 : 0;
       return fv < p.factor1 * bv ? 0 : 1;
     }
-    default: {  // Beamer alpha/beta
-      if (cur == 0) return (long long)(mf * (unsigned long long)p.alpha) > m_u ? 1 : 0;
+    default: {  // Beamer alpha/beta; BFS_SCHED_BEAMER_STAY: BU->TD also needs the TD->BU test to fail
+      const bool td_bu = (long long)(mf * (unsigned long long)p.alpha) > m_u;
+      if (cur == 0) return td_bu ? 1 : 0;
       const bool small = nf * (unsigned long long)p.beta < (unsigned long long)p.n;
-      return (small && nf < prev_nf) ? 0 : 1;
+      const bool stay = p.schedule == BFS_SCHED_BEAMER_STAY && td_bu;
+      return (small && nf < prev_nf && !stay) ? 0 : 1;
     }
   }
 }

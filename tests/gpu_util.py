@@ -7,6 +7,7 @@ import oracle
 
 SCHEDULES = {
     "beamer": dict(schedule=0),
+    "beamer_stay": dict(schedule=7),
     "topdown": dict(schedule=1),
     "bottomup": dict(schedule=2),
     "alternate": dict(schedule=3),

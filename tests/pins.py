@@ -431,7 +431,7 @@ def pin_level_counters_first_hit(lib):
 
 
 def pin_directions_worked(lib):
-    """Both direction rules against the hand-worked levels of
+    """The direction rules against the hand-worked levels of
     tests/golden/directions_worked.txt (Sec. IV-B)."""
     from tests.golden_io import read_directions
 
@@ -443,7 +443,7 @@ def pin_directions_worked(lib):
         if rule == "paper":
             got = g.directions(src, d, "paper", factor0=a, factor1=b)
         else:
-            got = g.directions(src, d, "beamer", alpha=int(a), beta=int(b))
+            got = g.directions(src, d, rule, alpha=int(a), beta=int(b))
         if list(got) != want:
             return False
     return True

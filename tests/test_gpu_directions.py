@@ -12,6 +12,8 @@ from tests.gpu_util import assert_same, gpu_bfs, gpu_graph, need_cuda
 pytestmark = pytest.mark.gpu
 
 RULES = [
+    ("beamer_stay", dict(alpha=15, beta=18)),
+    ("beamer_stay", dict(alpha=2, beta=5)),
     ("beamer", dict(alpha=15, beta=18)),
     ("beamer", dict(alpha=2, beta=5)),
     ("beamer", dict(alpha=200, beta=60)),
@@ -44,7 +46,7 @@ def graphs():
                                                     for r, p in RULES])
 def test_device_directions_follow_rule(graphs, rule, params):
     for name, n, src, dst, og in graphs:
-        opts = dict(schedule=0 if rule == "beamer" else 5, **params)
+        opts = dict(schedule={"beamer": 0, "beamer_stay": 7, "paper": 5}[rule], **params)
         g = gpu_graph(n, src, dst, th=16, **opts)
         rng = np.random.default_rng(len(name))
         mask = (np.diff(og.csr()[0]) > 0).astype(np.uint8)

@@ -45,6 +45,9 @@ MUTANTS = [
     ("paper_back_flipped", "!(fvd < factor1 * bv)", "!(fvd > factor1 * bv)"),
     ("beamer_no_shrink_test", "q[L] * beta < (int64_t)g->n && q[L] < q_prev", "q[L] * beta < (int64_t)g->n"),
     ("beamer_mu_all_edges", "m_u = m_total - seen_m;", "m_u = m_total;"),
+    ("stay_guard_dropped", "if (rule == ORC_RULE_BEAMER_STAY && fv[L] * alpha > m_u) next = 1;", ""),
+    ("stay_guard_ge", "if (rule == ORC_RULE_BEAMER_STAY && fv[L] * alpha > m_u) next = 1;",
+     "if (rule == ORC_RULE_BEAMER_STAY && fv[L] * alpha >= m_u) next = 1;"),
     ("directions_seen_after", "    seen_v += q[L];\n    seen_m += fv[L];\n", ""),
     ("subgraph_U_from_source_class", "if (unvisited && in_x > 0) U += 1;", "if (unvisited && out_x > 0) U += 1;"),
     ("subgraph_q_unfiltered", "if (depth[v] == L && out_x > 0) {", "if (depth[v] == L && is_del == src_del[x]) {"),
