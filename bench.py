@@ -4,8 +4,8 @@ on one GB300, GTEPS as the harmonic mean over 64 seeded sources.
 
 Workload (default): RMAT scale 26 (67,108,864 vertices, edge factor 16, a,b,c,d =
 .57,.19,.19,.05, ids permuted, self-loops and duplicates removed), degree
-threshold TH = 64, Beamer alpha = 15 / beta = 18, 64 seeded non-isolated sources,
-one query at a time through the persistent level-loop kernel.  A step is one BFS
+threshold TH = 64, direction rule Beamer-stay with alpha = 10 / beta = 18, 64
+seeded non-isolated sources, one query at a time through the persistent level-loop kernel.  A step is one BFS
 from each of the 64 sources.  GTEPS per run = unique undirected edges of the
 traversed component / device time of the run (CUDA events on the launching
 stream); the reported value is their harmonic mean.  The graph build is set-up,
@@ -808,7 +808,7 @@ def serving_extras(stream):
 
 def config_of(name, w, info=None):
     c = {"workload": name, "graph": "RMAT" if w["kind"] == "rmat" else "Erdos-Renyi", "scale": w["scale"],
-         "n": 1 << w["scale"], "th": w["th"], "schedule": "beamer_stay", "alpha": 15, "beta": 18,
+         "n": 1 << w["scale"], "th": w["th"], "schedule": "beamer_stay", "alpha": 10, "beta": 18,
          "sources": N_SOURCES,
          "graph_seed": w["seed"], "source_seed": w["src_seed"],
          "l2": "inputs larger than L2 and L2 flushed (256 MiB write) before every timed run"}

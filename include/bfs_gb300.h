@@ -72,7 +72,7 @@ typedef struct bfs_options {
   int32_t edges_on_device;  /* bfs_build_graph: 1 if src/dst are device pointers, 0 if host. */
   int32_t schedule;         /* BFS_SCHED_* (default BFS_SCHED_BEAMER_STAY) */
   uint64_t schedule_mask;   /* for BFS_SCHED_MASK */
-  int32_t alpha;            /* Beamer alpha (default 15) */
+  int32_t alpha;            /* Beamer alpha (default 10) */
   int32_t beta;             /* Beamer beta (default 18) */
   double factor0;           /* BFS_SCHED_PAPER: forward->backward when FV > factor0 * BV (default 0.5) */
   double factor1;           /* BFS_SCHED_PAPER: backward->forward when FV < factor1 * BV (default 1e-7) */

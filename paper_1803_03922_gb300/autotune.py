@@ -118,7 +118,7 @@ def tune(evaluate_for_th: Callable[[int], Callable[[Dict[str, object]], float]],
     """Full search.  evaluate_for_th(th) returns an evaluate(options) for a graph
     built with that threshold; directions_for_th(th, options) returns the
     per-level directions the options produce on a representative source."""
-    defaults = dict(defaults or {"schedule": BEAMER_STAY, "alpha": 15, "beta": 18, "blocks_per_sm": 2})
+    defaults = dict(defaults or {"schedule": BEAMER_STAY, "alpha": 10, "beta": 18, "blocks_per_sm": 2})
     trials: list = []
     baseline_t = None
     per_th = {}

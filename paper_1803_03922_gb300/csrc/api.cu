@@ -201,7 +201,7 @@ extern "C" int bfs_options_default(bfs_options* opt) {
   opt->edges_on_device = 0;
   opt->schedule = BFS_SCHED_BEAMER_STAY;
   opt->schedule_mask = 0;
-  opt->alpha = 15;
+  opt->alpha = 10;
   opt->beta = 18;
   opt->factor0 = 0.5;
   opt->factor1 = 1e-7;

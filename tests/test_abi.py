@@ -40,7 +40,7 @@ def test_options_default_and_errors_without_gpu():
     import paper_1803_03922_gb300 as bfs
 
     o = bfs.bfs_options_default()
-    assert (o.th, o.alpha, o.beta, o.schedule, o.td_parent) == (64, 15, 18, 7, 1)
+    assert (o.th, o.alpha, o.beta, o.schedule, o.td_parent) == (64, 10, 18, 7, 1)
     assert o.barrier_timeout_ms == 2000
     h = ctypes.c_void_p()
     lib = bfs._load()

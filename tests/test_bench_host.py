@@ -58,7 +58,7 @@ def test_workload_descriptions():
     for name, w in bench.WORKLOADS.items():
         c = bench.config_of(name, w)
         assert c["workload"] == name and c["n"] == 1 << w["scale"]
-        assert c["sources"] == bench.N_SOURCES and c["alpha"] == 15 and c["beta"] == 18
+        assert c["sources"] == bench.N_SOURCES and c["alpha"] == 10 and c["schedule"] == "beamer_stay" and c["beta"] == 18
         if w["kind"] == "rmat":
             assert c["edge_factor"] == 16 and c["abcd"] == [0.57, 0.19, 0.19, 0.05]
         else:

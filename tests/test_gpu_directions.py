@@ -12,6 +12,7 @@ from tests.gpu_util import assert_same, gpu_bfs, gpu_graph, need_cuda
 pytestmark = pytest.mark.gpu
 
 RULES = [
+    ("beamer_stay", dict(alpha=10, beta=18)),
     ("beamer_stay", dict(alpha=15, beta=18)),
     ("beamer_stay", dict(alpha=2, beta=5)),
     ("beamer", dict(alpha=15, beta=18)),
