@@ -597,6 +597,30 @@ def batched_vs_single(g, sources, batches=8):
     out["single_qps"] = 64 * batches / ms * 1e3
     out["single_gteps_aggregate"] = edges / (ms / 1e3) / 1e9
     out["speedup"] = out["batched_qps"] / out["single_qps"]
+    # the same queries grouped for batching (bfs_batch_order: by the degree sum of
+    # each source's neighbours), parents included
+    qs = np.asarray(sources[:64 * batches], dtype=np.int32)
+    grouped = qs[bfs.bfs_batch_order(g.handle, qs)]
+    b = bfs.Batch(g, with_parents=True)
+    depth = torch.empty((64, n), dtype=torch.uint8, device="cuda")
+    parent = torch.empty((64, n), dtype=torch.int32, device="cuda")
+    for i in range(2):
+        b.run(grouped[64 * i:64 * (i + 1)], depth, parent)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(batches):
+        b.run(grouped[64 * i:64 * (i + 1)], depth, parent)
+    e1.record()
+    torch.cuda.synchronize()
+    b.wait()
+    ms = e0.elapsed_time(e1)
+    out["batched_grouped_qps"] = 64 * batches / ms * 1e3
+    out["gteps_aggregate_grouped"] = edges / (ms / 1e3) / 1e9
+    out["speedup_grouped"] = out["batched_grouped_qps"] / out["single_qps"]
+    b.close()
+    del depth, parent
+    torch.cuda.empty_cache()
     # the batched schedule autotuned (Beamer alpha of the union frontier), then timed as above
     from paper_1803_03922_gb300.autotune import tune_batch_alpha
 

@@ -265,6 +265,18 @@ int bfs_run_batch(bfs_batch* b, const int32_t* sources, int32_t k, uint8_t* dept
 /* Synchronizes `stream`; status of the context's most recent batch. */
 int bfs_batch_wait(bfs_batch* b, struct CUstream_st* stream);
 
+/* Groups queries for batching (not in the paper).  Writes to order[0..k) a
+ * permutation of 0..k-1 that sorts the sources by the degree sum of their
+ * neighbours, largest first (ties keep their order); 0 for an isolated source.
+ * That sum is the row entries of a query's second frontier: queries with
+ * similar sums reach the graph's big levels at the same level, so batches cut
+ * from consecutive runs of the order scan shorter rows in their backward levels.
+ * sources: host array of k caller ids (k >= 0); order: host array of k.  Reads
+ * the graph on `stream` and synchronizes it.  BFS_ERR_INVALID for a NULL
+ * pointer, k < 0 or a source outside [0, n). */
+int bfs_batch_order(const bfs_graph* g, const int32_t* sources, int32_t k, int32_t* order,
+                    struct CUstream_st* stream);
+
 void bfs_batch_free(bfs_batch* b);
 
 /* ---- Serving loop: continuous batching of queries over device-resident graphs. ----

@@ -150,6 +150,7 @@ def _load():
     lib.bfs_batch_wait.argtypes = [c_vp, c_vp]
     lib.bfs_batch_free.argtypes = [c_vp]
     lib.bfs_batch_free.restype = None
+    lib.bfs_batch_order.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp]
     lib.bfs_degree_class_stats.argtypes = [c_vp, c_vp, c_i32, c_vp, c_vp]
     lib.bfs_server_options_default.argtypes = [ctypes.POINTER(bfs_server_options)]
     lib.bfs_server_options_default.restype = None
@@ -335,6 +336,15 @@ def bfs_batch_wait(b, stream=None):
 def bfs_batch_free(b):
     if b:
         _load().bfs_batch_free(b)
+
+
+def bfs_batch_order(g, sources, stream=None):
+    """Permutation (int32 numpy array) grouping the sources for batching: by the
+    degree sum of each source's neighbours, largest first."""
+    src = np.ascontiguousarray(sources, dtype=np.int32)
+    order = np.empty(src.size, dtype=np.int32)
+    _check(_load().bfs_batch_order(g, _ptr(src), src.size, _ptr(order), _stream(stream)))
+    return order
 
 
 def bfs_degree_class_stats(g, ths, stream=None):

@@ -16,8 +16,10 @@
 // the next delegate chunk list and counts the frontier for the direction choice
 // (Beamer alpha on vertex counts).  Depth is uint8 per (query, vertex), 255 =
 // unreached; a depth above 254 is an overflow error.
+#include <algorithm>
 #include <climits>
 #include <cstring>
+#include <vector>
 #include <new>
 
 #include "bfs_internal.cuh"
@@ -977,4 +979,65 @@ extern "C" void bfs_batch_free(bfs_batch* b) {
   cudaDeviceSynchronize();
   batch_free_all(b);
   delete b;
+}
+
+namespace bfsgb {
+namespace {
+
+// One warp per query: the degree sum of the source's neighbours (0 for an
+// isolated source), the size of the query's second frontier in entries.
+__global__ void k_order_keys(const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ deg, const int32_t* __restrict__ internal_of, int32_t n_ni,
+                             const int32_t* __restrict__ src, int32_t k, unsigned long long* __restrict__ key) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < k; j += nwarps) {
+    const int u = internal_of[src[j]];
+    unsigned long long s = 0;
+    if (u >= 0 && u < n_ni)
+      for (int64_t e = off[u] + lane; e < off[u + 1]; e += 32) s += (unsigned long long)deg[col[e]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) key[j] = s;
+  }
+}
+
+}  // namespace
+}  // namespace bfsgb
+
+extern "C" int bfs_batch_order(const bfs_graph* g, const int32_t* sources, int32_t k, int32_t* order,
+                               struct CUstream_st* stream) {
+  using namespace bfsgb;
+  if (!g || (k > 0 && (!sources || !order))) return fail(BFS_ERR_INVALID, "graph, sources or order is NULL");
+  if (k < 0) return fail(BFS_ERR_INVALID, "k must be >= 0");
+  for (int32_t j = 0; j < k; ++j)
+    if (sources[j] < 0 || sources[j] >= g->n) return fail(BFS_ERR_INVALID, "source out of range");
+  if (k == 0) return BFS_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != g->device) cudaSetDevice(g->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* dsrc = nullptr;
+  unsigned long long* dkey = nullptr;
+  std::vector<unsigned long long> key((size_t)k);
+  cudaError_t e = cudaMalloc(&dsrc, sizeof(int32_t) * (size_t)k);
+  if (e == cudaSuccess) e = cudaMalloc(&dkey, sizeof(unsigned long long) * (size_t)k);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dsrc, sources, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 4096);
+    k_order_keys<<<blocks, 256, 0, s>>>(g->off, g->col, g->deg, g->internal_of, g->n_ni, dsrc, k, dkey);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(key.data(), dkey, sizeof(unsigned long long) * (size_t)k,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (dsrc) cudaFree(dsrc);
+  if (dkey) cudaFree(dkey);
+  if (prev >= 0 && prev != g->device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return cuda_fail(e, "bfs_batch_order");
+  std::vector<int32_t> idx((size_t)k);
+  for (int32_t j = 0; j < k; ++j) idx[(size_t)j] = j;
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return key[(size_t)a] > key[(size_t)b]; });
+  std::memcpy(order, idx.data(), sizeof(int32_t) * (size_t)k);
+  return BFS_OK;
 }

@@ -188,3 +188,32 @@ def test_batch_isolated_and_overflow():
     assert int(dn[dn != 255].max()) == 150 and st.levels == 151
     d, p, st = b.run([301, 301], stats=True)  # isolated sources only: depth 0 is the deepest
     assert st.levels == 1 and st.logged_levels == 0 and st.pairs_reached == 0
+
+
+def test_batch_order_groups_by_second_frontier():
+    """bfs_batch_order returns a permutation sorted by the degree sum of each
+    source's neighbours (computed here from the oracle's CSR), largest first,
+    ties in input order; batches cut from it still equal the oracle."""
+    need_cuda()
+    import paper_1803_03922_gb300 as bfs
+
+    scale = 14
+    n = 1 << scale
+    src, dst = graphgen.rmat_host(scale, seed=1414)
+    og = oracle.Graph(n, src, dst)
+    off, col = og.csr()[:2]
+    deg = np.diff(off)
+    key = lambda s: int(deg[col[off[s]:off[s + 1]]].sum())
+    rng = np.random.default_rng(14)
+    sources = rng.integers(0, n, 200)  # isolated sources and repeats included
+    g = gpu_graph(n, src, dst, th=16)
+    order = bfs.bfs_batch_order(g.handle, sources)
+    assert sorted(order.tolist()) == list(range(len(sources)))
+    want = sorted(range(len(sources)), key=lambda j: (-key(sources[j]), j))
+    assert order.tolist() == want
+    grouped = sources[order]
+    for i in range(0, len(grouped), 64):
+        _batch_check(og, g, grouped[i:i + 64])
+    assert bfs.bfs_batch_order(g.handle, np.zeros(0, np.int32)).size == 0
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_batch_order(g.handle, np.array([n], np.int32))
