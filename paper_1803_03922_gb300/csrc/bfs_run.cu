@@ -449,9 +449,11 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
   const int64_t i = b * 32 + lane;
   const int u = i < qn ? Qc[i] : -1;
   int64_t beg = 0, deg = 0;
+  int cu = INT_MAX;  // the frontier vertex's caller id, loaded with its row bounds
   if (u >= 0 && BFS_IN(p, u, p.n_ni)) {
     beg = p.off[u];
     deg = p.deg[u];
+    if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) cu = p.caller_of[u];
   }
   const int64_t incl = warp_incl_scan(deg);
   const int64_t total = __shfl_sync(kFull, incl, 31);
@@ -471,7 +473,7 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
       }
       const int64_t ob = __shfl_sync(kFull, beg, pos);
       const int64_t ox = __shfl_sync(kFull, excl, pos);
-      ou[t] = __shfl_sync(kFull, u, pos);
+      ou[t] = __shfl_sync(kFull, cu, pos);
       v[t] = (e < total && BFS_IN(p, ob + (e - ox), p.nnz)) ? p.col[ob + (e - ox)] : -1;
     }
     unsigned un = 0;  // bit t: entry t meets an unvisited target
@@ -485,22 +487,14 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
     }
     if (!un) continue;
     found = true;
-    // the frontier vertex's caller id is loaded only for an edge into an unvisited
-    // target (most edges of a late forward level meet visited vertices)
-    int pcur[4], pc[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const bool a = ((un >> t) & 1u) && p.td_parent == BFS_TD_PARENT_ATOMICMIN;
-      pcur[t] = a ? __ldcg(p.parent_i + v[t]) : INT_MAX;
-      pc[t] = a ? p.caller_of[ou[t]] : INT_MAX;
-    }
+    // offers go out without reading the slot first (fire-and-forget reductions)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       if (!((un >> t) & 1u)) continue;
-      if (pcur[t] > pc[t]) atomicMin(p.parent_i + v[t], pc[t]);
+      if (p.td_parent == BFS_TD_PARENT_ATOMICMIN) atomicMin(p.parent_i + v[t], ou[t]);
       const unsigned bit = 1u << (v[t] & 31);
       uint32_t* nw = N + ((unsigned)v[t] >> 5);
-      if ((kSub || pcur[t] == INT_MAX) && (!(p.tuning & 1) || !(__ldcg(nw) & bit))) atomicOr(nw, bit);
+      if (!(p.tuning & 1) || !(__ldcg(nw) & bit)) atomicOr(nw, bit);
     }
   }
 }
