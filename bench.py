@@ -950,6 +950,15 @@ def main():
                    "e2e_single_call_gteps": e2e_single,
                    "e2e_single_call_ms_per_bfs_median": e2e_ms_single},
     }
+    if rank == 0 and not args.no_extras:
+        # the same graph and sources under plain Beamer alpha 15 / beta 18 (the
+        # direction rule before this build's default), for comparison
+        dw.g.set_options(schedule=0, alpha=15)
+        dw.timed(1, flush, stream)
+        tb = dw.timed(1, flush, stream)
+        line["detail"]["plain_beamer_a15"] = {"gteps": hmean(dw.gteps(tb)),
+                                              "ms_per_bfs_mean": 1e3 * statistics.mean(tb)}
+        dw.g.set_options(schedule=7, alpha=10)
     host_edges = dw.host_edges
     sources = dw.sources
     ce_dev = dw.ce
