@@ -548,6 +548,7 @@ def batched_vs_single(g, sources, batches=8):
     """64-lane batches against one query at a time on the same graph and sources:
     queries/s from CUDA events over `batches` x 64 queries, parents included, and
     the aggregate GTEPS (the queries' traversed component edges / time)."""
+    import numpy as np
     import torch
 
     import paper_1803_03922_gb300 as bfs
