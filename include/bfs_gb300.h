@@ -77,9 +77,10 @@ typedef struct bfs_options {
   double factor0;           /* BFS_SCHED_PAPER: forward->backward when FV > factor0 * BV (default 0.5) */
   double factor1;           /* BFS_SCHED_PAPER: backward->forward when FV < factor1 * BV (default 1e-7) */
   int32_t td_parent;        /* BFS_TD_PARENT_* (default ATOMICMIN) */
-  int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM: 0 or 2 = the 64-register build,
-                               3 = the 40-register build (3 CTAs of 512 threads per SM),
-                               1 = one CTA of 1024 threads per SM (64 registers) */
+  int32_t blocks_per_sm;    /* level-loop kernel CTAs per SM: 2 = the 64-register build (2 CTAs
+                               of 512 threads), 3 = the 40-register build (3 CTAs of 512 threads
+                               per SM), 1 = one CTA of 1024 threads per SM (64 registers);
+                               0 (default) = 1 above 2^24 non-isolated vertices, else 2 */
   int32_t barrier_timeout_ms; /* bound of every device-side grid-barrier wait (default 2000) */
   int32_t test_skip_barrier;  /* testing only: CTA 0 leaves before the first grid barrier, so the
                                  other CTAs' bounded wait expires and the run reports BFS_ERR_TIMEOUT */

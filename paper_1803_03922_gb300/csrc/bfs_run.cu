@@ -1859,7 +1859,10 @@ int configure_run(bfs_graph* g) {
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
   if (!coop) return fail(BFS_ERR_CUDA, "device does not support cooperative launch");
-  const int variant = g->opt.blocks_per_sm == 3 ? 3 : (g->opt.blocks_per_sm == 1 ? 1 : 2);
+  // 0 = by size: one 1024-thread CTA per SM once the non-isolated vertices pass
+  // 2^24 (measured faster there: RMAT-26 -1.8 %, ER-2^26 -1.1 %), else two of 512
+  const int bps = g->opt.blocks_per_sm != 0 ? g->opt.blocks_per_sm : (g->n_ni > (1 << 24) ? 1 : 2);
+  const int variant = bps == 3 ? 3 : (bps == 1 ? 1 : 2);
   if (variant == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<3, kThreads>, kThreads, 0);
   else if (variant == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<1, 2 * kThreads>, 2 * kThreads, 0);
   else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_level_loop<2, kThreads>, kThreads, 0);
