@@ -440,8 +440,8 @@ __device__ __forceinline__ void td_edge4(const BfsParams& p, const uint32_t* __r
 }
 
 // 32 normal-queue entries: lane i owns vertex Qc[b*32+i]; the warp walks the
-// concatenation of the 32 rows 32 entries at a time (entry e belongs to the lane
-// whose inclusive degree prefix first exceeds e).
+// concatenation of the 32 rows 128 entries at a time, four per lane (entry e
+// belongs to the lane whose inclusive degree prefix first exceeds e).
 template <bool kSub = false>
 __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, const int32_t* __restrict__ Qc,
                          int64_t qn, int64_t b, uint32_t* __restrict__ N, bool& found, unsigned allow = 3u) {
@@ -459,7 +459,7 @@ __device__ void td_batch(const BfsParams& p, const uint32_t* __restrict__ Vc, co
   const int64_t total = __shfl_sync(kFull, incl, 31);
   const int64_t excl = incl - deg;
   // up to four entries per lane per step (entries base + lane + 32 t), their
-  // column loads, probes and parent reads in flight together
+  // column loads and visited probes in flight together
   for (int64_t base = 0; base < total; base += 128) {
     int v[4], ou[4];
 #pragma unroll
