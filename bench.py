@@ -728,7 +728,8 @@ def serving_bench(stream, rates=SERVE_RATES, duration_s=1.5, single_cap=2000, ma
     Erdos-Renyi 2^22 with average degree 16): Poisson arrivals at each rate, uniform
     over graphs and over each graph's non-isolated sources; the server against the
     same arrivals served one at a time.  Also a saturation run (every query
-    arrives at once): the server's peak queries/s."""
+    arrives at once): the server's peak queries/s, with its default grouped
+    batches and with batches in arrival order."""
     import torch
 
     import paper_1803_03922_gb300 as bfs
@@ -757,6 +758,13 @@ def serving_bench(stream, rates=SERVE_RATES, duration_s=1.5, single_cap=2000, ma
     out["saturation_one_at_a_time"] = one_at_a_time(graphs, sources, sat[:single_cap], stream)
     out["server_stats"] = srv.stats()
     srv.close()
+    # the same saturation run with batches taken in arrival order (group_batches off)
+    fifo = bfs.Server(max_concurrent=max_concurrent, max_lanes=64, with_parents=True, group_batches=False)
+    for g in graphs:
+        fifo.add_graph(g)
+    serve_open_loop(fifo, graphs, sources, pools, serve_trace(20000, 400, len(graphs), SERVE_SOURCES, 1))
+    out["saturation_server_arrival_order"] = serve_open_loop(fifo, graphs, sources, pools, sat)
+    fifo.close()
     del pools
     for g in graphs:
         g.close()

@@ -310,7 +310,10 @@ typedef struct bfs_server_options {
   int32_t single_path;        /* 1: few waiting queries of a graph run the single-source level loop */
   int32_t single_max;         /* at most this many waiting queries (1..4; 0 = 3) run back to back on
                                  the level loop rather than as a batch */
-  int32_t reserved[6];        /* zero */
+  int32_t group_batches;      /* 1 (default): when more than max_lanes queries of a graph wait, a
+                                 batch takes the oldest one and the max_lanes-1 nearest it by
+                                 bfs_batch_order's key among the oldest 256; 0: arrival order */
+  int32_t reserved[5];        /* zero */
 } bfs_server_options;
 
 typedef struct bfs_server_done {

@@ -91,7 +91,8 @@ class bfs_batch_stats(ctypes.Structure):
 class bfs_server_options(ctypes.Structure):
     _fields_ = [("max_concurrent", c_i32), ("max_lanes", c_i32), ("with_parents", c_i32),
                 ("contexts_per_graph", c_i32), ("hbm_reserve_bytes", c_i64), ("hbm_budget_bytes", c_i64),
-                ("single_path", c_i32), ("single_max", c_i32), ("reserved", c_i32 * 6)]
+                ("single_path", c_i32), ("single_max", c_i32), ("group_batches", c_i32),
+                ("reserved", c_i32 * 5)]
 
 
 class bfs_server_done(ctypes.Structure):
@@ -536,7 +537,7 @@ class Server:
 
     def __init__(self, max_concurrent: int = 2, max_lanes: int = 64, with_parents: bool = True,
                  contexts_per_graph: int = 0, hbm_reserve_bytes: int = 0, hbm_budget_bytes: int = 0,
-                 single_path: bool = True, single_max: int = 3):
+                 single_path: bool = True, single_max: int = 3, group_batches: bool = True):
         o = bfs_server_options_default()
         o.max_concurrent = max_concurrent
         o.max_lanes = max_lanes
@@ -546,6 +547,7 @@ class Server:
         o.hbm_budget_bytes = hbm_budget_bytes
         o.single_path = 1 if single_path else 0
         o.single_max = single_max
+        o.group_batches = 1 if group_batches else 0
         self.with_parents = with_parents
         self.graphs = []
         self._live = {}  # ticket -> (depth, parent) kept alive until reported

@@ -1003,6 +1003,17 @@ __global__ void k_order_keys(const int64_t* __restrict__ off, const int32_t* __r
 }
 
 }  // namespace
+
+// Keys of bfs_batch_order for k sources already on the device (dsrc), into the
+// device array dkey; asynchronous on s.
+int order_keys_async(const bfs_graph* g, const int32_t* dsrc, int32_t k, unsigned long long* dkey, cudaStream_t s) {
+  if (k <= 0) return BFS_OK;
+  const int blocks = (int)std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 4096);
+  k_order_keys<<<blocks, 256, 0, s>>>(g->off, g->col, g->deg, g->internal_of, g->n_ni, dsrc, k, dkey);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? BFS_OK : cuda_fail(e, "order keys");
+}
+
 }  // namespace bfsgb
 
 extern "C" int bfs_batch_order(const bfs_graph* g, const int32_t* sources, int32_t k, int32_t* order,
@@ -1023,11 +1034,7 @@ extern "C" int bfs_batch_order(const bfs_graph* g, const int32_t* sources, int32
   cudaError_t e = cudaMalloc(&dsrc, sizeof(int32_t) * (size_t)k);
   if (e == cudaSuccess) e = cudaMalloc(&dkey, sizeof(unsigned long long) * (size_t)k);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dsrc, sources, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    const int blocks = (int)std::min<int64_t>(((int64_t)k * 32 + 255) / 256, 4096);
-    k_order_keys<<<blocks, 256, 0, s>>>(g->off, g->col, g->deg, g->internal_of, g->n_ni, dsrc, k, dkey);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess && order_keys_async(g, dsrc, k, dkey, s) != BFS_OK) e = cudaErrorLaunchFailure;
   if (e == cudaSuccess) e = cudaMemcpyAsync(key.data(), dkey, sizeof(unsigned long long) * (size_t)k,
                                             cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -37,11 +37,17 @@ using bfsgb::cuda_fail;
 using bfsgb::fail;
 using bfsgb::RunHeader;
 
+namespace bfsgb {
+// msbfs.cu: the keys of bfs_batch_order for k device-resident sources.
+int order_keys_async(const bfs_graph* g, const int32_t* dsrc, int32_t k, unsigned long long* dkey, cudaStream_t s);
+}  // namespace bfsgb
+
 namespace {
 
 constexpr int kMaxLanes = 64;
 constexpr int kMaxConcurrent = 8;
 constexpr int kMaxSingle = 4;  // single-source runs per launch of a graph's level-loop context
+constexpr int kGroupWindow = 256;  // oldest waiting queries of a graph that a grouped batch picks from
 
 int64_t now_ns() {
   return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -108,6 +114,12 @@ struct bfs_server {
   std::vector<std::unique_ptr<Context>> ctx;
   int ctas_in_use = 0;
   std::thread worker;
+  // grouped batches: a stream and buffers for the keys of a window of waiting queries
+  cudaStream_t order_stream = nullptr;
+  int32_t* order_src_h = nullptr;              // pinned [kGroupWindow]
+  unsigned long long* order_key_h = nullptr;   // pinned [kGroupWindow]
+  int32_t* order_src_d = nullptr;              // device [kGroupWindow]
+  unsigned long long* order_key_d = nullptr;   // device [kGroupWindow]
 };
 
 namespace {
@@ -305,6 +317,59 @@ void launch(bfs_server* s, Context& c) {
   finish(s, c, rc, now_ns());
 }
 
+void release_order(bfs_server* s) {
+  if (s->order_stream) cudaStreamDestroy(s->order_stream);
+  if (s->order_src_h) cudaFreeHost(s->order_src_h);
+  if (s->order_key_h) cudaFreeHost(s->order_key_h);
+  if (s->order_src_d) cudaFree(s->order_src_d);
+  if (s->order_key_d) cudaFree(s->order_key_d);
+  s->order_stream = nullptr;
+  s->order_src_h = nullptr;
+  s->order_key_h = nullptr;
+  s->order_src_d = nullptr;
+  s->order_key_d = nullptr;
+}
+
+// Grouped batch of graph gid when more than cap queries wait: the oldest waiting
+// query and the cap-1 queries whose grouping keys (bfs_batch_order's) lie nearest
+// it among the oldest kGroupWindow, as ascending positions in the waiting queue.
+// Empty: take the queue in arrival order.  Only the worker removes waiting
+// queries, so the window's positions hold while the lock is released.
+std::vector<int> group_pick(bfs_server* s, int gid, int cap) {
+  std::vector<int> pick;
+  if (!s->order_stream) return pick;
+  int W = 0;
+  const bfs_graph* g = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    const std::deque<Query>& w = s->graphs[gid].waiting;
+    if ((int)w.size() <= cap) return pick;
+    W = (int)std::min<size_t>(w.size(), (size_t)kGroupWindow);
+    for (int i = 0; i < W; ++i) s->order_src_h[i] = w[(size_t)i].source;
+    g = s->graphs[gid].g;
+  }
+  cudaError_t e = cudaMemcpyAsync(s->order_src_d, s->order_src_h, sizeof(int32_t) * W, cudaMemcpyHostToDevice,
+                                  s->order_stream);
+  if (e != cudaSuccess || bfsgb::order_keys_async(g, s->order_src_d, W, s->order_key_d, s->order_stream) != BFS_OK)
+    return pick;
+  e = cudaMemcpyAsync(s->order_key_h, s->order_key_d, sizeof(unsigned long long) * W, cudaMemcpyDeviceToHost,
+                      s->order_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->order_stream);
+  if (e != cudaSuccess) return pick;
+  std::vector<int> idx((size_t)W);
+  for (int i = 0; i < W; ++i) idx[(size_t)i] = i;
+  std::stable_sort(idx.begin(), idx.end(),
+                   [&](int a, int b) { return s->order_key_h[a] > s->order_key_h[b]; });
+  int pos = 0;
+  while (idx[(size_t)pos] != 0) ++pos;
+  int start = pos - cap / 2;
+  if (start > W - cap) start = W - cap;
+  if (start < 0) start = 0;
+  pick.assign(idx.begin() + start, idx.begin() + start + cap);
+  std::sort(pick.begin(), pick.end());
+  return pick;
+}
+
 void schedule(bfs_server* s) {
   for (;;) {
     std::vector<int> order;
@@ -345,10 +410,15 @@ void schedule(bfs_server* s) {
     if (!c) return;
     c->ctas = ctas;
     s->ctas_in_use += ctas;
+    const int cap = c->single ? s->opt.single_max : s->opt.max_lanes;
+    const std::vector<int> pick = c->single ? std::vector<int>() : group_pick(s, c->gid, cap);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       std::deque<Query>& w = s->graphs[c->gid].waiting;
-      const int cap = c->single ? s->opt.single_max : s->opt.max_lanes;
+      if (!pick.empty()) {
+        for (int i : pick) c->q.push_back(w[(size_t)i]);
+        for (size_t j = pick.size(); j-- > 0;) w.erase(w.begin() + pick[j]);
+      }
       while (!w.empty() && (int)c->q.size() < cap) {
         c->q.push_back(w.front());
         w.pop_front();
@@ -393,6 +463,7 @@ extern "C" void bfs_server_options_default(bfs_server_options* opt) {
   opt->contexts_per_graph = 2;
   opt->single_path = 1;
   opt->single_max = 3;
+  opt->group_batches = 1;
 }
 
 extern "C" int64_t bfs_server_now_ns(void) { return now_ns(); }
@@ -416,6 +487,7 @@ extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out
   if (!o.single_path) o.single_max = 0;
   else if (o.single_max == 0) o.single_max = 3;
   if (o.hbm_reserve_bytes < 0 || o.hbm_budget_bytes < 0) return fail(BFS_ERR_INVALID, "byte limits must be >= 0");
+  if (o.group_batches != 0 && o.group_batches != 1) return fail(BFS_ERR_INVALID, "group_batches must be 0 or 1");
   int dev = 0, cap = 0;
   const cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "bfs_server_create");
@@ -428,9 +500,22 @@ extern "C" int bfs_server_create(const bfs_server_options* opt, bfs_server** out
   s->device = dev;
   s->capacity = cap;
   s->slice = cap / o.max_concurrent;
+  if (o.group_batches) {
+    cudaError_t ge = cudaStreamCreateWithFlags(&s->order_stream, cudaStreamNonBlocking);
+    if (ge == cudaSuccess) ge = cudaMallocHost((void**)&s->order_src_h, sizeof(int32_t) * kGroupWindow);
+    if (ge == cudaSuccess) ge = cudaMallocHost((void**)&s->order_key_h, sizeof(unsigned long long) * kGroupWindow);
+    if (ge == cudaSuccess) ge = cudaMalloc((void**)&s->order_src_d, sizeof(int32_t) * kGroupWindow);
+    if (ge == cudaSuccess) ge = cudaMalloc((void**)&s->order_key_d, sizeof(unsigned long long) * kGroupWindow);
+    if (ge != cudaSuccess) {
+      release_order(s);
+      delete s;
+      return cuda_fail(ge, "server grouping buffers");
+    }
+  }
   try {
     s->worker = std::thread(worker_main, s);
   } catch (...) {
+    release_order(s);
     delete s;
     return fail(BFS_ERR_OOM, "cannot start the worker thread");
   }
@@ -522,6 +607,7 @@ extern "C" void bfs_server_destroy(bfs_server* s) {
   s->cv_done.notify_all();
   if (s->worker.joinable()) s->worker.join();
   while (!s->ctx.empty()) drop_context(s, s->ctx.size() - 1);
+  release_order(s);
   delete s;
 }
 

@@ -217,3 +217,32 @@ def test_lone_queries_and_depth_overflow(single_path):
     assert_same(r["depth"].cpu().numpy(), want_d[0], "depth after an overflow")
     assert_same(r["parent"].cpu().numpy(), want_p[0], "parent after an overflow")
     srv.close()
+
+
+@pytest.mark.parametrize("group", [True, False])
+def test_grouped_batches_serve_the_oldest_first(group):
+    """With more than max_lanes queries waiting, a grouped batch (the default)
+    takes the oldest waiting query and the queries nearest it by the grouping
+    key; in arrival order (group_batches off) batches are runs of consecutive
+    tickets.  Either way every result equals the oracle."""
+    bfs, srv, gs, ogs = _setup(max_concurrent=1, max_lanes=16, group_batches=group)
+    rng = np.random.default_rng(21)
+    q = [(0, int(s)) for s in rng.integers(0, gs[0].n, 200)]
+    tickets = [srv.submit(gid, s) for gid, s in q]
+    recs = {r["ticket"]: r for r in srv.drain()}
+    _check_oracle(ogs, q, [recs[t] for t in tickets])
+    launches = {}
+    for t in tickets:
+        launches.setdefault(recs[t]["t_launch_ns"], []).append(t)
+    remaining = sorted(tickets)
+    for t_launch in sorted(launches):
+        members = sorted(launches[t_launch])
+        assert members[0] == remaining[0], "a launch skipped the oldest waiting query"
+        if not group:
+            i = remaining.index(members[0])
+            assert members == remaining[i:i + len(members)]
+        for t in members:
+            remaining.remove(t)
+        assert len(members) <= 16
+    assert not remaining
+    srv.close()
